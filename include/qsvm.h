@@ -1,0 +1,153 @@
+/*
+ * qsvm.h -- C ABI of libqsvm: GB300-native quantum-kernel estimation for QSVMs
+ * (after arXiv 2405.02630, "Validating Large-Scale Quantum Machine Learning:
+ * Efficient Simulation of Quantum Support Vector Machines Using Tensor Networks").
+ *
+ * The library computes quantum-kernel matrices
+ *     K(x_i, x_j) = |<psi(x_j)|psi(x_i)>|^2 = |<0^n| U^dagger(x_j) U(x_i) |0^n>|^2
+ * (Sec. 2, Eq. 3 and Eq. 4) for the n-qubit linear-chain feature map of Sec. 3.2
+ * (CNOTs in a linear topology, one qubit per feature).  One repetition of U(x):
+ * H on every qubit; RZ(2 x_k) on every qubit; then for k = 0..n-2 the block
+ * CNOT(k,k+1) . RZ_{k+1}(2 (pi - x_k)(pi - x_{k+1})) . CNOT(k,k+1).
+ * RZ(theta) = diag(exp(-i theta/2), exp(+i theta/2)).  reps repetitions.
+ *
+ * Each state U(x)|0^n> is built exactly (no truncation) as a matrix product
+ * state of bond dimension chi = 2^reps, and every kernel entry is the overlap of
+ * two such states contracted along the chain (the tensor-network kernel of
+ * Algorithm 2, with the chain's fixed left-to-right contraction order).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named X, mps, K, logK are DEVICE pointers owned by the caller
+ *     (e.g. allocated through PyTorch); the library never allocates, frees or
+ *     retains them.  Buffers handed to the library must be 16-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls only enqueue work on it and return; they never synchronise, except
+ *     qsvm_device_status(), which says so.
+ *   - Return value: QSVM_OK (0) or a negative qsvm_status.  Argument errors are
+ *     detected on the host before anything is enqueued.  qsvm_last_error()
+ *     returns a thread-local message for the last failing call on this thread.
+ *   - Kernels never trap.  A wait inside a kernel that exceeds its bound makes
+ *     the kernel record QSVM_ERR_TIMEOUT in a device status word and return;
+ *     qsvm_device_status() reads it.
+ *   - All indices are 64-bit; matrices are row-major with explicit leading
+ *     dimensions (in elements).
+ */
+#ifndef QSVM_H
+#define QSVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum qsvm_status {
+  QSVM_OK = 0,
+  QSVM_ERR_ARG = -1,            /* bad pointer, size, alignment or leading dim  */
+  QSVM_ERR_CHI = -2,            /* reps outside 1..3 (chi = 2^reps > 8)          */
+  QSVM_ERR_CUDA = -3,           /* a CUDA runtime call or launch failed          */
+  QSVM_ERR_TIMEOUT = -4,        /* a bounded in-kernel wait ran out              */
+  QSVM_ERR_UNIMPLEMENTED = -5,  /* valid request this build does not provide     */
+  QSVM_ERR_WORKSPACE = -6       /* caller workspace smaller than required        */
+};
+
+/* ---- arithmetic of the pair contraction --------------------------------- */
+enum qsvm_precision {
+  /* FP64 everywhere: the parity path. */
+  QSVM_FP64 = 0,
+  /* Plain FP32 site tensors and FP32 environment on the CUDA cores; exact
+   * power-of-two renormalisation.  Fastest; relative error grows with n. */
+  QSVM_FP32 = 1,
+  /* Split FP32: every site tensor and environment entry is hi + lo, with hi on a
+   * fixed binary grid so that hi*hi products and their short sums are exact in
+   * FP32 FMAs, and the lo terms carried as FP32 corrections.  Accuracy near
+   * FP64 (|dK| ~ 1e-8 at n = 784) at FP32-pipe speed. */
+  QSVM_FP32_SPLIT = 2
+};
+
+/* ---- MPS storage ---------------------------------------------------------
+ * An MPS buffer holds n_points * n_qubits site records, point-major:
+ * record (i, k) starts at byte (i * n_qubits + k) * qsvm_mps_record_bytes().
+ * The feature map ends with a diagonal layer, so the physical index of site k
+ * equals the last-repetition spin carried on its right bond: with the right
+ * bond index u = 2p + s and left bond index t = 2q + c, the tensor
+ * A_k[sigma][t][u] is nonzero only when sigma == s, and the record stores the
+ * four chi/2 x chi/2 blocks a_cs[q][p] = A_k[s][2q+c][2p+s], block index
+ * b = 2c + s, each row-major over (q, p):
+ *   QSVM_FP64        complex128 (re, im) per entry;
+ *   QSVM_FP32        complex64 per entry;
+ *   QSVM_FP32_SPLIT  per block: chi^2/4 complex64 "hi" entries (re and im on
+ *                    the 2^-11 grid), then chi^2/4 complex64 "lo" entries.
+ * Site 0 has a left bond of dimension 1 (only t = 0 is nonzero); the last site
+ * has a right bond of dimension 2 holding the physical index (u = sigma, p = 0).
+ * The layout is private to this library: produce it with qsvm_build_mps. */
+size_t qsvm_mps_record_bytes(int32_t reps, int32_t precision);
+size_t qsvm_mps_bytes(int32_t n_qubits, int32_t reps, int64_t n_points, int32_t precision);
+
+/* qsvm_build_mps -- exact MPS of U(x)|0^n> for every row of X (Sec. 3.2 circuit;
+ * the state whose overlaps Eq. 4 needs).
+ *   X          device, n_points x n_qubits float64, row-major (features = angles,
+ *              already scaled as the caller wants; the paper uses PCA-reduced,
+ *              scaled pixels, Sec. 3.2).
+ *   precision  storage format of the output records (the build itself is FP64).
+ *   mps        device output, at least qsvm_mps_bytes(...) bytes (mps_bytes).
+ * Gate by gate in FP64, site by site: H and RZ act on the physical index; the
+ * commuting CNOT.RZ.CNOT blocks of one repetition act as a bond-2 diagonal MPO
+ * that copies each spin onto the bond and applies exp(-i theta Z_k Z_{k+1}),
+ * theta = (pi - x_k)(pi - x_{k+1}), on the right-hand site.
+ * Errors: QSVM_ERR_ARG (null, n_qubits < 2, n_points < 1, mps_bytes too small,
+ * misaligned), QSVM_ERR_CHI (reps outside 1..3), QSVM_ERR_CUDA. */
+int32_t qsvm_build_mps(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
+                       void* mps, size_t mps_bytes, void* stream);
+
+/* qsvm_kernel_gram -- symmetric train x train kernel matrix (Algorithm 2 with
+ * its symmetrisation step): K[i*ldk + j] = |<psi_j|psi_i>|^2 for all i, j.
+ * Only pairs i <= j are contracted (the diagonal too, it is computed rather
+ * than set to 1) and K[j][i] is written as a bit-exact copy of K[i][j].
+ *   mps   device, built by qsvm_build_mps with the same n_qubits, reps, precision.
+ *   K     device float64, n_points rows, ldk >= n_points.
+ *   logK  device float64 or NULL; if given, ln K (-inf where the amplitude is 0);
+ *         ldl >= n_points.  K underflows to 0 below ~1e-308 while logK stays exact.
+ * Errors: QSVM_ERR_ARG, QSVM_ERR_CHI, QSVM_ERR_CUDA. */
+int32_t qsvm_kernel_gram(const void* mps, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
+                         double* K, int64_t ldk, double* logK, int64_t ldl, void* stream);
+
+/* qsvm_kernel_cross -- test x train kernel (Algorithms 1-3 with datasize1 !=
+ * datasize2; never symmetrised): K[i*ldk + j] = |<psi(train_j)|psi(test_i)>|^2.
+ *   mps_a  device MPS of the n_a test points; mps_b of the n_b train points.
+ *   K      device float64, n_a rows, ldk >= n_b; logK as above (ldl >= n_b).
+ * Errors: as qsvm_kernel_gram. */
+int32_t qsvm_kernel_cross(const void* mps_a, int64_t n_a, const void* mps_b, int64_t n_b, int32_t n_qubits,
+                          int32_t reps, int32_t precision, double* K, int64_t ldk, double* logK, int64_t ldl,
+                          void* stream);
+
+/* ---- sharding the symmetric Gram over independent workers ----------------
+ * The upper-triangle pair tiles of a Gram are independent (Sec. 5: pairs are
+ * distributed evenly over GPUs and the results gathered).  Tiles are numbered
+ * row-major over the upper triangle of a T x T tile grid, T = ceil(n_points /
+ * qsvm_gram_tile_dim()).  qsvm_gram_partition splits [0, tiles) into `world`
+ * contiguous ranges of near-equal pair count; qsvm_kernel_gram_tiles computes
+ * one range (writing both K[i][j] and its mirror for every pair in it).  These
+ * three are pure host functions except qsvm_kernel_gram_tiles. */
+int32_t qsvm_gram_tile_dim(int32_t reps, int32_t precision);
+int64_t qsvm_gram_num_tiles(int64_t n_points, int32_t reps, int32_t precision);
+int32_t qsvm_gram_partition(int64_t n_points, int32_t reps, int32_t precision, int32_t world, int32_t rank,
+                            int64_t* tile_begin, int64_t* tile_end);
+int32_t qsvm_kernel_gram_tiles(const void* mps, int64_t n_points, int32_t n_qubits, int32_t reps,
+                               int32_t precision, int64_t tile_begin, int64_t tile_end, double* K, int64_t ldk,
+                               double* logK, int64_t ldl, void* stream);
+
+/* ---- diagnostics --------------------------------------------------------- */
+/* Reads (and, if clear != 0, resets) the device status words written by this
+ * library's kernels on the current device: QSVM_OK or QSVM_ERR_TIMEOUT.
+ * Synchronises `stream`.  Returns QSVM_OK or QSVM_ERR_CUDA. */
+int32_t qsvm_device_status(void* stream, int32_t clear, int32_t* status_out);
+const char* qsvm_last_error(void);
+const char* qsvm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSVM_H */

@@ -1,0 +1,176 @@
+// build_mps.cu -- K1: exact MPS of U(x)|0^n> for every data point, in FP64.
+//
+// The circuit is the linear-chain feature map of arXiv 2405.02630 Sec. 3.2 (one
+// qubit per feature, CNOTs in a linear topology); per repetition: H on every
+// qubit, RZ(2 x_k) on every qubit, then CNOT(k,k+1) . RZ_{k+1}(2 theta_k) .
+// CNOT(k,k+1) for k = 0..n-2 with theta_k = (pi - x_k)(pi - x_{k+1}).
+//
+// Every gate acts on at most the bond next to a site, so each site tensor can be
+// built on its own from (x_{k-1}, x_k): the builder starts each site in |0>
+// with bond dimension 1 and applies, per repetition,
+//   H        on the physical index;
+//   RZ(2x_k) on the physical index: diag(e^{-i x_k}, e^{+i x_k});
+//   the CNOT.RZ.CNOT chain of that repetition as one bond-2 diagonal MPO.  The
+//   block on (k-1, k) equals exp(-i theta_{k-1} Z_{k-1} Z_k); as an MPO the left
+//   site copies its spin onto the shared bond (right bond grows by a bit b equal
+//   to the spin) and the right site multiplies by exp(-i theta z(a) z(sigma))
+//   where a is that copied spin (left bond grows by the bit a).
+// After reps repetitions both bonds have dimension 2^reps (site 0: left bond 1;
+// last site: right bond 1), with rep 1 in the most significant bit.  The last
+// repetition's copied bit is the low bit of the right bond and equals the
+// physical index, which is what the block layout of the record relies on.
+#include "qsvm_common.cuh"
+
+namespace qsvm {
+
+struct cd {
+  double re, im;
+};
+__device__ __forceinline__ cd cmul(cd a, cd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+// Store one complex entry (q, p) of block b in the record, in the requested format.
+template <int CHI, int PREC>
+__device__ __forceinline__ void store_entry(uint8_t* rec, int b, int q, int p, cd v) {
+  using Rec = Record<CHI, PREC>;
+  constexpr int H = CHI / 2;
+  uint8_t* blk = rec + b * Rec::kBlockBytes;
+  const int e = q * H + p;
+  if constexpr (PREC == QSVM_FP64) {
+    reinterpret_cast<double2*>(blk)[e] = make_double2(v.re, v.im);
+  } else if constexpr (PREC == QSVM_FP32) {
+    reinterpret_cast<float2*>(blk)[e] = make_float2(__double2float_rn(v.re), __double2float_rn(v.im));
+  } else {
+    // hi: nearest multiple of 2^-kGridT (exact in double and in float since
+    // |v| <= 1); lo: the remainder rounded to float.
+    constexpr double s = (double)(1 << kGridT);
+    const double hr = rint(v.re * s) / s, hi = rint(v.im * s) / s;
+    reinterpret_cast<float2*>(blk)[e] = make_float2((float)hr, (float)hi);
+    reinterpret_cast<float2*>(blk)[H * H + e] =
+        make_float2(__double2float_rn(v.re - hr), __double2float_rn(v.im - hi));
+  }
+}
+
+// Row t of the site tensor: v[sigma][u] after all repetitions.
+// LAST: the site has no right neighbour (no copy onto a right bond).
+template <int R, bool LAST>
+__device__ __forceinline__ void site_row(int t, bool has_left, cd rz0, cd zzp, cd zzm, cd (&v)[2][1 << R]) {
+  constexpr int CHI = 1 << R;
+  const double r2 = 0.70710678118654752440;
+#pragma unroll
+  for (int r = 0; r < CHI; ++r) v[0][r] = v[1][r] = cd{0.0, 0.0};
+  v[0][0] = cd{1.0, 0.0};
+#pragma unroll
+  for (int m = 1; m <= R; ++m) {
+    const int d = LAST ? 1 : (1 << (m - 1));  // right-bond dimension before this rep
+    // H on the physical index
+#pragma unroll
+    for (int r = 0; r < d; ++r) {
+      const cd a = v[0][r], b = v[1][r];
+      v[0][r] = cd{(a.re + b.re) * r2, (a.im + b.im) * r2};
+      v[1][r] = cd{(a.re - b.re) * r2, (a.im - b.im) * r2};
+    }
+    // RZ(2 x_k): sigma = 0 gets e^{-i x}, sigma = 1 gets e^{+i x}
+    const cd rz1 = cd{rz0.re, -rz0.im};
+#pragma unroll
+    for (int r = 0; r < d; ++r) {
+      v[0][r] = cmul(v[0][r], rz0);
+      v[1][r] = cmul(v[1][r], rz1);
+    }
+    // ZZ block with the left neighbour: exp(-i theta z(a) z(sigma)), a = bit of t
+    if (has_left) {
+      const int a = (t >> (R - m)) & 1;
+      const cd p0 = a ? zzm : zzp;             // sigma = 0: exp(-i theta z(a))
+      const cd p1 = cd{p0.re, -p0.im};         // sigma = 1: exp(+i theta z(a))
+#pragma unroll
+      for (int r = 0; r < d; ++r) {
+        v[0][r] = cmul(v[0][r], p0);
+        v[1][r] = cmul(v[1][r], p1);
+      }
+    }
+    // copy the spin onto the right bond: v'[sigma][2r + sigma] = v[sigma][r]
+    if (!LAST) {
+#pragma unroll
+      for (int r = d - 1; r >= 0; --r) {
+        const cd a = v[0][r], b = v[1][r];
+        v[0][2 * r] = a;
+        v[0][2 * r + 1] = cd{0.0, 0.0};
+        v[1][2 * r] = cd{0.0, 0.0};
+        v[1][2 * r + 1] = b;
+      }
+    }
+  }
+}
+
+template <int R, int PREC>
+__global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict__ X, int64_t n_points, int n,
+                                                        uint8_t* __restrict__ mps) {
+  constexpr int CHI = 1 << R;
+  using Rec = Record<CHI, PREC>;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= n_points * (int64_t)n) return;
+  const int64_t i = gid / n;
+  const int k = (int)(gid - i * n);
+  const double xk = X[i * n + k];
+  double sx, cx;
+  sincos(xk, &sx, &cx);
+  const cd rz0 = cd{cx, -sx};  // e^{-i x_k}
+  cd zzp = cd{1.0, 0.0}, zzm = cd{1.0, 0.0};
+  const bool has_left = k > 0;
+  if (has_left) {
+    const double th = (kPi - X[i * n + k - 1]) * (kPi - xk);
+    double st, ct;
+    sincos(th, &st, &ct);
+    zzp = cd{ct, -st};  // a = 0: z(a) = +1 -> exp(-i theta) for sigma = 0
+    zzm = cd{ct, st};   // a = 1: z(a) = -1 -> exp(+i theta) for sigma = 0
+  }
+  uint8_t* rec = mps + gid * Rec::kBytes;
+  const bool last = (k == n - 1);
+  for (int t = 0; t < CHI; ++t) {
+    cd v[2][CHI];
+    if (!has_left && t > 0) {
+#pragma unroll
+      for (int u = 0; u < CHI; ++u) v[0][u] = v[1][u] = cd{0.0, 0.0};
+    } else if (last) {
+      site_row<R, true>(t, has_left, rz0, zzp, zzm, v);
+    } else {
+      site_row<R, false>(t, has_left, rz0, zzp, zzm, v);
+    }
+    const int c = t & 1, q = t >> 1;
+#pragma unroll
+    for (int u = 0; u < CHI; ++u) {
+      const int s = u & 1, p = u >> 1;
+      cd val;
+      if (last) val = (u < 2) ? v[u][0] : cd{0.0, 0.0};
+      else val = v[s][u];
+      store_entry<CHI, PREC>(rec, 2 * c + s, q, p, val);
+    }
+  }
+}
+
+template <int R, int PREC>
+static cudaError_t launch_build_t(const double* X, int64_t N, int n, void* mps, cudaStream_t st) {
+  const int64_t total = N * (int64_t)n;
+  const int threads = 256;
+  const int64_t blocks = (total + threads - 1) / threads;
+  build_mps_kernel<R, PREC><<<(unsigned)blocks, threads, 0, st>>>(X, N, n, static_cast<uint8_t*>(mps));
+  return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t launch_build_r(const double* X, int64_t N, int n, int prec, void* mps, cudaStream_t st) {
+  switch (prec) {
+    case QSVM_FP64: return launch_build_t<R, QSVM_FP64>(X, N, n, mps, st);
+    case QSVM_FP32: return launch_build_t<R, QSVM_FP32>(X, N, n, mps, st);
+    default: return launch_build_t<R, QSVM_FP32_SPLIT>(X, N, n, mps, st);
+  }
+}
+
+cudaError_t launch_build_mps(const double* X, int64_t N, int n, int reps, int prec, void* mps, cudaStream_t st) {
+  switch (reps) {
+    case 1: return launch_build_r<1>(X, N, n, prec, mps, st);
+    case 2: return launch_build_r<2>(X, N, n, prec, mps, st);
+    default: return launch_build_r<3>(X, N, n, prec, mps, st);
+  }
+}
+
+}  // namespace qsvm

@@ -1,0 +1,127 @@
+// qsvm_common.cuh -- device-side helpers shared by the libqsvm kernels.
+//
+// Site-record layout (see include/qsvm.h): four chi/2 x chi/2 blocks per site,
+// block b = 2c + s holds a_cs[q][p] = A[s][2q+c][2p+s]; entries complex.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qsvm.h"
+
+namespace qsvm {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Binary grids of the split-FP32 format.  Tensor hi parts sit on 2^-kGridT;
+// environment hi parts on 2^-kGridE after renormalisation to max |.| < 1;
+// intermediate (A^T E) hi parts on 2^-kGridX(chi).  The exactness argument
+// (every hi*hi partial sum stays below 2^24 grid units) is spelled out in
+// pair_contract.cu.
+constexpr int kGridT = 11;
+constexpr int kGridE = 10;
+__host__ __device__ constexpr int grid_x(int chi) { return chi >= 8 ? 8 : 9; }
+
+template <int CHI, int PREC>
+struct Record {
+  static constexpr int H = CHI / 2;                    // block side
+  static constexpr int kEntries = H * H;               // complex entries per block
+  static constexpr int kEntryBytes = (PREC == QSVM_FP64) ? 16 : 8;
+  static constexpr int kBlockBytes = kEntries * kEntryBytes * (PREC == QSVM_FP32_SPLIT ? 2 : 1);
+  static constexpr int kBytes = 4 * kBlockBytes;
+};
+
+inline size_t record_bytes(int chi, int prec) {
+  const size_t h2 = (size_t)(chi / 2) * (chi / 2);
+  const size_t entry = (prec == QSVM_FP64) ? 16 : 8;
+  return 4 * h2 * entry * (prec == QSVM_FP32_SPLIT ? 2 : 1);
+}
+
+// Launch arguments of the pair-tile kernels.
+struct TileArgs {
+  const uint8_t* mpsA;   // MPS of the row points (i)
+  const uint8_t* mpsB;   // MPS of the column points (j)
+  int64_t nA, nB;
+  int n;                 // sites (qubits)
+  int symmetric;         // 1: upper-triangle tiles of a Gram (mpsA == mpsB)
+  int64_t tile_begin;    // first linear tile index of this launch
+  int64_t tiles_j;       // tiles per row (cross) or per side (symmetric)
+  double* K;
+  int64_t ldk;
+  double* logK;          // nullable
+  int64_t ldl;
+};
+
+// ---------------------------------------------------------------- PTX ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// One bulk (TMA, untiled) copy global -> shared, completion counted in bytes on
+// the mbarrier.  dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: true when the phase completed, false after
+// `limit_ns` nanoseconds of waiting (the caller then records a timeout).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
+constexpr uint64_t kWaitLimitNs = 4000000000ull;    // 4 s: a chunk copy takes microseconds
+constexpr uint64_t kDrainLimitNs = 1000000000ull;   // after a timeout, wait at most 1 s more
+
+// ----------------------------------------------------------- scalars -----
+// Exact scaling by 2^-e for |e| <= 126 (single power-of-two multiply).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// Round to the nearest multiple of 2^-g (ties to even) without leaving FP32:
+// (v + 1.5*2^(23-g)) - 1.5*2^(23-g), valid for |v| < 2^(22-g).
+template <int G>
+__device__ __forceinline__ float grid_round(float v) {
+  constexpr float C = 1.5f * (float)(1 << (23 - G));
+  return __fsub_rn(__fadd_rn(v, C), C);
+}
+
+}  // namespace qsvm

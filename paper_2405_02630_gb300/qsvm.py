@@ -1,0 +1,203 @@
+"""Thin ctypes binding of libqsvm (include/qsvm.h), same entry-point names.
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if libqsvm.so is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqsvm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "qsvm.h")
+
+QSVM_OK = 0
+QSVM_ERR_ARG = -1
+QSVM_ERR_CHI = -2
+QSVM_ERR_CUDA = -3
+QSVM_ERR_TIMEOUT = -4
+QSVM_ERR_UNIMPLEMENTED = -5
+QSVM_ERR_WORKSPACE = -6
+
+QSVM_FP64 = 0
+QSVM_FP32 = 1
+QSVM_FP32_SPLIT = 2
+PRECISIONS = {"fp64": QSVM_FP64, "fp32": QSVM_FP32, "fp32_split": QSVM_FP32_SPLIT}
+
+
+class QsvmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"qsvm error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+_i32, _i64, _sz, _vp, _dp = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p
+_SIGS = {
+    "qsvm_mps_record_bytes": (_sz, [_i32, _i32]),
+    "qsvm_mps_bytes": (_sz, [_i32, _i32, _i64, _i32]),
+    "qsvm_build_mps": (_i32, [_dp, _i64, _i32, _i32, _i32, _vp, _sz, _vp]),
+    "qsvm_kernel_gram": (_i32, [_vp, _i64, _i32, _i32, _i32, _dp, _i64, _dp, _i64, _vp]),
+    "qsvm_kernel_cross": (_i32, [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _dp, _i64, _dp, _i64, _vp]),
+    "qsvm_gram_tile_dim": (_i32, [_i32, _i32]),
+    "qsvm_gram_num_tiles": (_i64, [_i64, _i32, _i32]),
+    "qsvm_gram_partition": (_i32, [_i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "qsvm_kernel_gram_tiles": (_i32, [_vp, _i64, _i32, _i32, _i32, _i64, _i64, _dp, _i64, _dp, _i64, _vp]),
+    "qsvm_device_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
+    "qsvm_last_error": (ctypes.c_char_p, []),
+    "qsvm_version": (ctypes.c_char_p, []),
+}
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/qsvm.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qsvm_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Load libqsvm.so (raises if it is missing: no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing; build it with paper_2405_02630_gb300.build")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != QSVM_OK:
+        raise QsvmError(rc, lib().qsvm_last_error().decode())
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- queries ---
+def qsvm_mps_record_bytes(reps: int, precision) -> int:
+    return int(lib().qsvm_mps_record_bytes(reps, _prec(precision)))
+
+
+def qsvm_mps_bytes(n_qubits: int, reps: int, n_points: int, precision) -> int:
+    return int(lib().qsvm_mps_bytes(n_qubits, reps, n_points, _prec(precision)))
+
+
+def qsvm_gram_tile_dim(reps: int, precision) -> int:
+    return int(lib().qsvm_gram_tile_dim(reps, _prec(precision)))
+
+
+def qsvm_gram_num_tiles(n_points: int, reps: int, precision) -> int:
+    return int(lib().qsvm_gram_num_tiles(n_points, reps, _prec(precision)))
+
+
+def qsvm_gram_partition(n_points: int, reps: int, precision, world: int, rank: int):
+    b, e = _i64(0), _i64(0)
+    _check(lib().qsvm_gram_partition(n_points, reps, _prec(precision), world, rank, ctypes.byref(b),
+                                     ctypes.byref(e)))
+    return int(b.value), int(e.value)
+
+
+# ---------------------------------------------------------------- compute ---
+def qsvm_build_mps(X, reps: int, precision, mps=None, stream=None):
+    """X: CUDA float64 (n_points, n_qubits), contiguous.  Returns the MPS buffer
+    (a CUDA uint8 tensor of qsvm_mps_bytes bytes; allocated if not given)."""
+    import torch
+    assert X.is_cuda and X.dtype == torch.float64 and X.is_contiguous() and X.dim() == 2
+    N, n = X.shape
+    prec = _prec(precision)
+    need = qsvm_mps_bytes(n, reps, N, prec)
+    if mps is None:
+        mps = torch.empty(max(need, 16), dtype=torch.uint8, device=X.device)
+    _check(lib().qsvm_build_mps(_ptr(X), N, n, reps, prec, _ptr(mps), mps.numel() * mps.element_size(),
+                                _stream(stream)))
+    return mps
+
+
+def qsvm_kernel_gram(mps, n_points: int, n_qubits: int, reps: int, precision, K=None, logK=False, stream=None,
+                     device=None):
+    """Symmetric Gram from an MPS buffer.  Returns (K, logK or None)."""
+    import torch
+    dev = device or mps.device
+    if K is None:
+        K = torch.empty((n_points, n_points), dtype=torch.float64, device=dev)
+    L = torch.empty((n_points, n_points), dtype=torch.float64, device=dev) if logK is True else (logK or None)
+    _check(lib().qsvm_kernel_gram(_ptr(mps), n_points, n_qubits, reps, _prec(precision), _ptr(K), K.stride(0),
+                                  _ptr(L), L.stride(0) if L is not None else 0, _stream(stream)))
+    return K, L
+
+
+def qsvm_kernel_gram_tiles(mps, n_points: int, n_qubits: int, reps: int, precision, tile_begin: int, tile_end: int,
+                           K, logK=None, stream=None):
+    _check(lib().qsvm_kernel_gram_tiles(_ptr(mps), n_points, n_qubits, reps, _prec(precision), tile_begin, tile_end,
+                                        _ptr(K), K.stride(0), _ptr(logK), logK.stride(0) if logK is not None else 0,
+                                        _stream(stream)))
+    return K, logK
+
+
+def qsvm_kernel_cross(mps_a, n_a: int, mps_b, n_b: int, n_qubits: int, reps: int, precision, K=None, logK=False,
+                      stream=None):
+    """Test x train kernel: K[i, j] = |<psi(train_j)|psi(test_i)>|^2.  Returns (K, logK or None)."""
+    import torch
+    dev = mps_a.device
+    if K is None:
+        K = torch.empty((n_a, n_b), dtype=torch.float64, device=dev)
+    L = torch.empty((n_a, n_b), dtype=torch.float64, device=dev) if logK is True else (logK or None)
+    _check(lib().qsvm_kernel_cross(_ptr(mps_a), n_a, _ptr(mps_b), n_b, n_qubits, reps, _prec(precision), _ptr(K),
+                                   K.stride(0), _ptr(L), L.stride(0) if L is not None else 0, _stream(stream)))
+    return K, L
+
+
+def qsvm_device_status(clear: bool = True, stream=None) -> int:
+    v = _i32(0)
+    _check(lib().qsvm_device_status(_stream(stream), 1 if clear else 0, ctypes.byref(v)))
+    return int(v.value)
+
+
+def qsvm_last_error() -> str:
+    return lib().qsvm_last_error().decode()
+
+
+def qsvm_version() -> str:
+    return lib().qsvm_version().decode()
+
+
+# ------------------------------------------------------------ convenience ---
+def gram(X, reps: int, precision, logK: bool = False, stream=None):
+    """Build the MPS of every row of X and return its Gram (K, logK or None)."""
+    N, n = X.shape
+    mps = qsvm_build_mps(X, reps, precision, stream=stream)
+    return qsvm_kernel_gram(mps, N, n, reps, precision, logK=logK, stream=stream)
+
+
+def cross(X_test, X_train, reps: int, precision, logK: bool = False, stream=None):
+    ma = qsvm_build_mps(X_test, reps, precision, stream=stream)
+    mb = qsvm_build_mps(X_train, reps, precision, stream=stream)
+    return qsvm_kernel_cross(ma, X_test.shape[0], mb, X_train.shape[0], X_test.shape[1], reps, precision, logK=logK,
+                             stream=stream)

@@ -1,0 +1,91 @@
+"""The C-ABI library loads, exports every symbol include/qsvm.h declares, and its
+pure-host logic (argument checks, sizes, tile partition) behaves -- no GPU needed:
+every call here returns before touching CUDA."""
+import ctypes
+
+import pytest
+
+from paper_2405_02630_gb300 import qsvm
+
+
+def test_exports_every_declared_symbol():
+    L = qsvm.lib()
+    names = qsvm.header_symbols()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(qsvm._SIGS), "binding and header disagree"
+
+
+def test_record_and_mps_bytes():
+    # chi^2 complex entries per site (half of the dense 2 chi^2 are structural zeros)
+    for reps, chi in ((1, 2), (2, 4), (3, 8)):
+        assert qsvm.qsvm_mps_record_bytes(reps, "fp64") == chi * chi * 16
+        assert qsvm.qsvm_mps_record_bytes(reps, "fp32") == chi * chi * 8
+        assert qsvm.qsvm_mps_record_bytes(reps, "fp32_split") == chi * chi * 16
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 8192 * 784 * 256
+    assert qsvm.qsvm_mps_record_bytes(4, "fp64") == 0
+    assert qsvm.qsvm_mps_record_bytes(2, 7) == 0
+
+
+def _call_gram(**kw):
+    a = dict(mps=16, n=16, nq=8, reps=2, prec=0, K=64, ldk=16, L=None, ldl=0)
+    a.update(kw)
+    return qsvm.lib().qsvm_kernel_gram(ctypes.c_void_p(a["mps"]), a["n"], a["nq"], a["reps"], a["prec"],
+                                       ctypes.c_void_p(a["K"]), a["ldk"], ctypes.c_void_p(a["L"]) if a["L"] else None,
+                                       a["ldl"], None)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(reps=0), qsvm.QSVM_ERR_CHI), (dict(reps=4), qsvm.QSVM_ERR_CHI), (dict(nq=1), qsvm.QSVM_ERR_ARG),
+    (dict(prec=3), qsvm.QSVM_ERR_ARG), (dict(n=0), qsvm.QSVM_ERR_ARG), (dict(mps=0), qsvm.QSVM_ERR_ARG),
+    (dict(mps=8), qsvm.QSVM_ERR_ARG), (dict(K=0), qsvm.QSVM_ERR_ARG), (dict(ldk=15), qsvm.QSVM_ERR_ARG),
+    (dict(L=64, ldl=3), qsvm.QSVM_ERR_ARG),
+])
+def test_gram_argument_errors(kw, code):
+    assert _call_gram(**kw) == code
+    assert qsvm.qsvm_last_error()
+
+
+def test_build_and_cross_argument_errors():
+    L = qsvm.lib()
+    v = ctypes.c_void_p
+    assert L.qsvm_build_mps(v(64), 4, 8, 2, 0, v(64), 10, None) == qsvm.QSVM_ERR_ARG  # mps_bytes too small
+    assert L.qsvm_build_mps(None, 4, 8, 2, 0, v(64), 1 << 20, None) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_build_mps(v(64), 4, 8, 5, 0, v(64), 1 << 20, None) == qsvm.QSVM_ERR_CHI
+    assert L.qsvm_kernel_cross(v(16), 4, v(16), 0, 8, 2, 0, v(64), 4, None, 0, None) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_kernel_cross(v(16), 4, v(16), 5, 8, 2, 0, v(64), 4, None, 0, None) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_kernel_gram_tiles(v(16), 16, 8, 2, 0, 0, 99, v(64), 16, None, 0, None) == qsvm.QSVM_ERR_ARG
+
+
+def _tile_pairs(b, N, T, td):
+    # row-major upper triangle of a T x T tile grid
+    r = 0
+    while b >= T - r:
+        b -= T - r
+        r += 1
+    ti, tj = r, r + b
+    ni, nj = min(td, N - ti * td), min(td, N - tj * td)
+    return ni * (ni + 1) // 2 if ti == tj else ni * nj
+
+
+@pytest.mark.parametrize("N,world", [(1, 1), (17, 2), (100, 3), (1000, 8), (8192, 4), (33, 7)])
+def test_gram_partition_covers_and_balances(N, world):
+    td = qsvm.qsvm_gram_tile_dim(2, "fp32_split")
+    T = -(-N // td)
+    total = qsvm.qsvm_gram_num_tiles(N, 2, "fp32_split")
+    assert total == T * (T + 1) // 2
+    ranges = [qsvm.qsvm_gram_partition(N, 2, "fp32_split", world, r) for r in range(world)]
+    assert ranges[0][0] == 0 and ranges[-1][1] == total
+    assert all(ranges[r][1] == ranges[r + 1][0] for r in range(world - 1))
+    pairs = [sum(_tile_pairs(b, N, T, td) for b in range(lo, hi)) for lo, hi in ranges]
+    assert sum(pairs) == N * (N + 1) // 2
+    if total >= 4 * world:
+        assert max(pairs) - min(pairs) <= 2 * td * td
+
+
+def test_partition_errors():
+    with pytest.raises(qsvm.QsvmError):
+        qsvm.qsvm_gram_partition(100, 2, 0, 2, 2)
+    with pytest.raises(qsvm.QsvmError):
+        qsvm.qsvm_gram_partition(0, 2, 0, 1, 0)

@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (|K_gpu - K_oracle|, elementwise):
+  FP64        1e-10  (the FP64 parity bar)
+  FP32_SPLIT  1e-6   (the low-precision bar; measured ~1e-8 at n = 784)
+  FP32        2e-5 for n <= 64 and 1e-4 at n = 784 (plain FP32 is the fast path
+              without compensation: its coherent rounding error grows with n)
+log K is compared where the oracle's K exceeds 1e-300.
+"""
+import numpy as np
+import pytest
+
+from paper_2405_02630_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32_split": 1e-6, "fp32": 2e-5}
+LOG_TOL = {"fp64": 1e-8, "fp32_split": 1e-5, "fp32": 1e-3}
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_02630_gb300 import qsvm
+    qsvm.lib()
+    return qsvm
+
+
+def _dev(X):
+    return torch.from_numpy(np.ascontiguousarray(X, dtype=np.float64)).cuda()
+
+
+def _decode_fp64(buf, N, n, reps):
+    """Site tensors A[i, k, sigma, t, u] from FP64 records (layout of include/qsvm.h)."""
+    chi = 2 ** reps
+    H = chi // 2
+    raw = buf.cpu().numpy().view(np.complex128).reshape(N, n, 4, H, H)
+    A = np.zeros((N, n, 2, chi, chi), complex)
+    for c in range(2):
+        for s in range(2):
+            for qq in range(H):
+                for p in range(H):
+                    A[:, :, s, 2 * qq + c, 2 * p + s] = raw[:, :, 2 * c + s, qq, p]
+    return A
+
+
+def _mps_state(A):
+    """Contract one point's site tensors A[k, sigma, t, u] to the 2^n state (qubit k = bit k)."""
+    n, _, chi, _ = A.shape
+    psi = np.zeros(2 ** n, complex)
+    for s in range(2 ** n):
+        v = np.zeros(chi, complex)
+        v[0] = 1.0
+        for k in range(n):
+            v = v @ A[k, (s >> k) & 1]
+        psi[s] = v.sum()  # last site: right bond carries sigma; A vanishes off u == sigma
+    return psi
+
+
+def _check(Kg, Ko, prec, what, LKg=None, LKo=None):
+    err = np.max(np.abs(Kg - Ko))
+    assert err <= TOL[prec], f"{what} {prec}: max|dK| = {err:.3e}"
+    if LKg is not None:
+        m = Ko > 1e-300
+        if m.any():
+            lerr = np.max(np.abs(LKg[m] - LKo[m]))
+            assert lerr <= LOG_TOL[prec], f"{what} {prec}: max|dlnK| = {lerr:.3e}"
+    return err
+
+
+# ------------------------------------------------------------- builder -----
+@pytest.mark.parametrize("reps", [1, 2, 3])
+@pytest.mark.parametrize("n", [2, 3, 7, 10])
+def test_build_mps_reproduces_state_vector(q, oracle, n, reps):
+    X = inputs.uniform_features(3, n, 1000 + 10 * n + reps)
+    buf = q.qsvm_build_mps(_dev(X), reps, "fp64")
+    torch.cuda.synchronize()
+    A = _decode_fp64(buf, 3, n, reps)
+    for i in range(3):
+        psi = _mps_state(A[i])
+        ref = oracle.sv_state(X[i], reps)
+        assert np.max(np.abs(psi - ref)) <= 1e-12
+
+
+def test_build_mps_lowprec_formats(q):
+    N, n, reps = 5, 33, 2
+    X = inputs.mnist_like_features(N, n, 77)
+    d = _dev(X)
+    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128)
+    f32 = q.qsvm_build_mps(d, reps, "fp32").cpu().numpy().view(np.complex64)
+    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.complex64).reshape(N * n, 4, 2, 4)
+    hi, lo = spl[:, :, 0, :].reshape(-1), spl[:, :, 1, :].reshape(-1)
+    assert np.array_equal(f32, f64.astype(np.complex64))
+    for part in (hi.real, hi.imag):
+        assert np.array_equal(np.round(part.astype(np.float64) * 2048) / 2048, part)
+    rec = hi.astype(np.complex128) + lo.astype(np.complex128)
+    assert np.max(np.abs(rec - f64)) <= 2 ** -34
+
+
+# ----------------------------------------------------------- small Grams ---
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split", "fp32"])
+def test_gram_cfg0_vs_statevector(q, oracle, prec):
+    X, _, n, reps = inputs.workload("cfg0_n8_r2_N16")
+    Ko = oracle.sv_gram(X, reps)
+    K, LK = q.gram(_dev(X), reps, prec, logK=True)
+    Kg = K.cpu().numpy()
+    _check(Kg, Ko, prec, "cfg0", LK.cpu().numpy(), np.log(np.maximum(Ko, 1e-320)))
+    assert np.array_equal(Kg, Kg.T)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split", "fp32"])
+@pytest.mark.parametrize("reps", [1, 2, 3])
+@pytest.mark.parametrize("N,n", [(1, 2), (17, 5), (100, 64), (37, 13)])
+def test_gram_vs_mps_oracle(q, oracle, prec, reps, N, n):
+    X = inputs.uniform_features(N, n, 7 * N + n + reps)
+    Ko, LKo = oracle.mps_gram(X, reps)
+    K, LK = q.gram(_dev(X), reps, prec, logK=True)
+    Kg = K.cpu().numpy()
+    _check(Kg, Ko, prec, f"gram N={N} n={n} reps={reps}", LK.cpu().numpy(), LKo)
+    assert np.array_equal(Kg, Kg.T)
+    assert q.qsvm_device_status() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split", "fp32"])
+def test_cross_vs_mps_oracle(q, oracle, prec):
+    n, reps = 64, 2
+    Xtr = inputs.uniform_features(53, n, 11)
+    Xte = inputs.uniform_features(29, n, 12)
+    Ko, LKo = oracle.mps_cross(Xte, Xtr, reps)
+    K, LK = q.cross(_dev(Xte), _dev(Xtr), reps, prec, logK=True)
+    _check(K.cpu().numpy(), Ko, prec, "cross", LK.cpu().numpy(), LKo)
+
+
+def test_cross_leading_dimension(q, oracle):
+    n, reps = 12, 2
+    Xa, Xb = inputs.uniform_features(9, n, 3), inputs.uniform_features(21, n, 4)
+    ma, mb = q.qsvm_build_mps(_dev(Xa), reps, "fp64"), q.qsvm_build_mps(_dev(Xb), reps, "fp64")
+    big = torch.full((9, 40), -7.0, dtype=torch.float64, device="cuda")
+    q.qsvm_kernel_cross(ma, 9, mb, 21, n, reps, "fp64", K=big[:, 5:26])
+    B = big.cpu().numpy()
+    Ko, _ = oracle.mps_cross(Xa, Xb, reps)
+    assert np.max(np.abs(B[:, 5:26] - Ko)) <= 1e-10
+    assert np.all(B[:, :5] == -7.0) and np.all(B[:, 26:] == -7.0)
+
+
+# ------------------------------------------------- n = 784 (paper's size) ---
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
+def test_gram_n784_mnist_like(q, oracle, prec):
+    X = inputs.mnist_like_features(40, 784, 2)
+    Ko, LKo = oracle.mps_gram(X, 2)
+    K, LK = q.gram(_dev(X), 2, prec, logK=True)
+    _check(K.cpu().numpy(), Ko, prec, "n784 gram", LK.cpu().numpy(), LKo)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split", "fp32"])
+def test_near_duplicates_n784(q, oracle, prec):
+    # kernel values spread over (0, 1): the regime where |dK| <= 1e-6 is not vacuous
+    base = inputs.mnist_like_features(24, 784, 21)
+    pert = inputs.near_duplicates(base, 22)
+    Ko, LKo = oracle.mps_cross(base, pert, 2)
+    assert np.diag(Ko).min() < 0.9 and np.diag(Ko).max() > 0.99
+    K, LK = q.cross(_dev(base), _dev(pert), 2, prec, logK=True)
+    tol = {"fp64": 1e-10, "fp32_split": 1e-6, "fp32": 1e-4}[prec]
+    err = np.max(np.abs(K.cpu().numpy() - Ko))
+    assert err <= tol, f"{prec}: max|dK| = {err:.3e}"
+
+
+def test_reps3_n784_logk(q, oracle):
+    X = inputs.mnist_like_features(6, 784, 31)
+    Ko, LKo = oracle.mps_gram(X, 3)
+    K, LK = q.gram(_dev(X), 3, "fp64", logK=True)
+    _check(K.cpu().numpy(), Ko, "fp64", "reps3 n784", LK.cpu().numpy(), LKo)
+    L = LK.cpu().numpy()
+    assert np.all(np.isfinite(L))
+    assert np.max(np.abs(L - LKo)) <= 1e-8  # log K exact even where K underflows
+
+
+# ----------------------------------------------------------- sharding ------
+def test_gram_tile_ranges_compose(q):
+    N, n, reps, prec = 70, 24, 2, "fp32_split"
+    X = _dev(inputs.uniform_features(N, n, 5))
+    mps = q.qsvm_build_mps(X, reps, prec)
+    Kfull, _ = q.qsvm_kernel_gram(mps, N, n, reps, prec)
+    Kpart = torch.full((N, N), float("nan"), dtype=torch.float64, device="cuda")
+    for r in range(3):
+        b, e = q.qsvm_gram_partition(N, reps, prec, 3, r)
+        q.qsvm_kernel_gram_tiles(mps, N, n, reps, prec, b, e, Kpart)
+    assert torch.equal(Kfull, Kpart)
+
+
+# ------------------------------------------- full size, sampled (bench config) ---
+def test_full_size_gram_sampled(q, oracle):
+    """n = 784, reps = 2, N = 8192, split FP32, in the launch the bench times:
+    bit-exact symmetry everywhere, and sampled entries against the oracle."""
+    X, _, n, reps = inputs.workload("gram_n784_r2_N8192")
+    N = X.shape[0]
+    K, LK = q.gram(_dev(X), reps, "fp32_split", logK=True)
+    torch.cuda.synchronize()
+    assert q.qsvm_device_status() == 0
+    assert torch.equal(K, K.T)
+    rng = np.random.default_rng(0)
+    di = rng.choice(N, 256, replace=False)
+    ia = np.concatenate([di, rng.integers(0, N, 256)])
+    ib = np.concatenate([di, rng.integers(0, N, 256)])
+    Ko, LKo = oracle.mps_pairs(X, X, ia, ib, reps)
+    Kg = K[torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda()].cpu().numpy()
+    LKg = LK[torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda()].cpu().numpy()
+    assert np.max(np.abs(Kg - Ko)) <= 1e-6
+    m = Ko > 1e-300
+    assert np.max(np.abs(LKg[m] - LKo[m])) <= 1e-5
