@@ -21,6 +21,9 @@ WORKLOADS = {
     "cfg2_n784_r2_N2048x1024": (784, 2, 2048, 1024, "mnist_like", 2),
     "cfg4_n784_r3_N8192": (784, 3, 8192, 0, "mnist_like", 4),
     "gram_n784_r2_N8192": (784, 2, 8192, 0, "mnist_like", 4),
+    # smaller cases of the same distribution, for profiler captures
+    "gram_n784_r2_N1024": (784, 2, 1024, 0, "mnist_like", 4),
+    "gram_n784_r3_N1024": (784, 3, 1024, 0, "mnist_like", 4),
 }
 
 
