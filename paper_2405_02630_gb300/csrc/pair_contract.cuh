@@ -289,17 +289,20 @@ struct Engine<CHI, QSVM_FP32> {
 //   step 2  E' = sum_c X conj(b):  hi(X) on 2^-GX (GX = 9, or 8 for chi = 8) with
 //           |X| <= chi * 2^{-reps/2} (<= 2.83), hi(b) on 2^-11, 4*(chi/2) real
 //           products  ->  < 8.4e6 units of 2^-(GX+11)  (2^24 = 1.68e7).
-// The lo terms (hi(a) lo(E) + lo(a) full(E), and the same for step 2) are
-// about 2^-11 of the result, so their FP32 rounding costs ~2^-35 relative per
-// site; nothing else is rounded.  This is the split hi+lo compensated product
-// carried out on the FP32 pipe.
+// The remaining terms use a = hi(a) + lo(a):
+//   a E = hi(a) hi(E) + hi(a) lo(E) + lo(a) full(E)      (step 1)
+//   X b = hi(X) hi(b) + full(X) lo(b) + lo(X) hi(b)      (step 2)
+// where full() is the rounded FP32 sum hi + lo.  Each correction is about 2^-11
+// of the result, so its FP32 rounding costs ~2^-35 relative per site; nothing
+// else is rounded.  This is the split hi+lo compensated product carried out on
+// the FP32 pipe: 12 FMAs per complex MAC.
 template <int CHI>
 struct Engine<CHI, QSVM_FP32_SPLIT> {
   static constexpr int H = CHI / 2;
   static constexpr int GX = grid_x(CHI);
   static constexpr int kRenormEvery = 1;  // built into site()
   using Rec = Record<CHI, QSVM_FP32_SPLIT>;
-  float2 Eh[2][H][H], El[2][H][H];
+  float2 Eh[2][H][H], El[2][H][H], Ef[2][H][H];  // Ef = fl(Eh + El)
   int L;
 
   __device__ __forceinline__ void init() {
@@ -308,20 +311,12 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
 #pragma unroll
       for (int q = 0; q < H; ++q)
 #pragma unroll
-        for (int r = 0; r < H; ++r) Eh[c][q][r] = El[c][q][r] = make_float2(0.f, 0.f);
-    Eh[0][0][0].x = 1.f;
+        for (int r = 0; r < H; ++r) Eh[c][q][r] = El[c][q][r] = Ef[c][q][r] = make_float2(0.f, 0.f);
+    Eh[0][0][0].x = Ef[0][0][0].x = 1.f;
     L = 0;
   }
 
   __device__ __forceinline__ void site(const uint8_t* ra, const uint8_t* rb) {
-    float2 Ef[2][H][H];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-      for (int q = 0; q < H; ++q)
-#pragma unroll
-        for (int r = 0; r < H; ++r)
-          Ef[c][q][r] = make_float2(__fadd_rn(Eh[c][q][r].x, El[c][q][r].x), __fadd_rn(Eh[c][q][r].y, El[c][q][r].y));
     float2 Nh[2][H][H], Nl[2][H][H];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -341,7 +336,7 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
         load_block_f<H>(pb, bh);
         load_block_f<H>(pb + H * H * 8, bl);
         // step 1: X[p][r] = sum_q a[q][p] E_c[q][r]
-        float2 Xh[H][H], Xl[H][H];
+        float2 Xh[H][H], Xl[H][H], Xf[H][H];
 #pragma unroll
         for (int p = 0; p < H; ++p) {
 #pragma unroll
@@ -364,10 +359,11 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
               li = __fmaf_rn(Al.x, ef.y, li);
               li = __fmaf_rn(Al.y, ef.x, li);
             }
-            const float xr = grid_round<GX>(__fadd_rn(hr, lr));
-            const float xi = grid_round<GX>(__fadd_rn(hi, li));
+            const float vr = __fadd_rn(hr, lr), vi = __fadd_rn(hi, li);
+            const float xr = grid_round<GX>(vr), xi = grid_round<GX>(vi);
             Xh[p][r] = make_float2(xr, xi);
             Xl[p][r] = make_float2(__fadd_rn(__fsub_rn(hr, xr), lr), __fadd_rn(__fsub_rn(hi, xi), li));
+            Xf[p][r] = make_float2(vr, vi);
           }
         }
         // step 2: N_s[p][pp] += sum_r X[p][r] conj(b[r][pp])
@@ -378,20 +374,19 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
             float hr = Nh[s][p][pp].x, hi = Nh[s][p][pp].y, lr = Nl[s][p][pp].x, li = Nl[s][p][pp].y;
 #pragma unroll
             for (int r = 0; r < H; ++r) {
-              const float2 X = Xh[p][r], Xo = Xl[p][r], B = bh[r][pp], Bl = bl[r][pp];
-              const float2 Bf = make_float2(__fadd_rn(B.x, Bl.x), __fadd_rn(B.y, Bl.y));
+              const float2 X = Xh[p][r], Xo = Xl[p][r], Xa = Xf[p][r], B = bh[r][pp], Bl = bl[r][pp];
               hr = __fmaf_rn(X.x, B.x, hr);
               hr = __fmaf_rn(X.y, B.y, hr);
               hi = __fmaf_rn(X.y, B.x, hi);
               hi = __fmaf_rn(-X.x, B.y, hi);
-              lr = __fmaf_rn(X.x, Bl.x, lr);
-              lr = __fmaf_rn(X.y, Bl.y, lr);
-              lr = __fmaf_rn(Xo.x, Bf.x, lr);
-              lr = __fmaf_rn(Xo.y, Bf.y, lr);
-              li = __fmaf_rn(X.y, Bl.x, li);
-              li = __fmaf_rn(-X.x, Bl.y, li);
-              li = __fmaf_rn(Xo.y, Bf.x, li);
-              li = __fmaf_rn(-Xo.x, Bf.y, li);
+              lr = __fmaf_rn(Xa.x, Bl.x, lr);
+              lr = __fmaf_rn(Xa.y, Bl.y, lr);
+              lr = __fmaf_rn(Xo.x, B.x, lr);
+              lr = __fmaf_rn(Xo.y, B.y, lr);
+              li = __fmaf_rn(Xa.y, Bl.x, li);
+              li = __fmaf_rn(-Xa.x, Bl.y, li);
+              li = __fmaf_rn(Xo.y, B.x, li);
+              li = __fmaf_rn(-Xo.x, B.y, li);
             }
             Nh[s][p][pp] = make_float2(hr, hi);
             Nl[s][p][pp] = make_float2(lr, li);
@@ -399,16 +394,18 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
         }
       }
     }
-    // renormalise by 2^-e (max |component| into [0.5, 1)) and re-split onto the E grid
+    // renormalise by 2^-e (max |component| of hi + lo into [0.5, 1)) and re-split onto the E grid
+    float2 V[2][H][H];
     float m = 0.f;
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
       for (int p = 0; p < H; ++p)
 #pragma unroll
-        for (int r = 0; r < H; ++r)
-          m = fmaxf(m, fmaxf(fabsf(__fadd_rn(Nh[s][p][r].x, Nl[s][p][r].x)),
-                             fabsf(__fadd_rn(Nh[s][p][r].y, Nl[s][p][r].y))));
+        for (int r = 0; r < H; ++r) {
+          V[s][p][r] = make_float2(__fadd_rn(Nh[s][p][r].x, Nl[s][p][r].x), __fadd_rn(Nh[s][p][r].y, Nl[s][p][r].y));
+          m = fmaxf(m, fmaxf(fabsf(V[s][p][r].x), fabsf(V[s][p][r].y)));
+        }
     int e = 0;
     if (m > 0.f && isfinite(m)) {
       frexpf(m, &e);
@@ -423,6 +420,8 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
               Nh[s][p][r].y *= pow2f(100);
               Nl[s][p][r].x *= pow2f(100);
               Nl[s][p][r].y *= pow2f(100);
+              V[s][p][r].x *= pow2f(100);
+              V[s][p][r].y *= pow2f(100);
             }
         L -= 100;
         e += 100;
@@ -435,12 +434,14 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
       for (int p = 0; p < H; ++p)
 #pragma unroll
         for (int r = 0; r < H; ++r) {
-          const float hs = __fmul_rn(Nh[s][p][r].x, sc), ls = __fmul_rn(Nl[s][p][r].x, sc);
-          const float hs2 = __fmul_rn(Nh[s][p][r].y, sc), ls2 = __fmul_rn(Nl[s][p][r].y, sc);
-          const float eh = grid_round<kGridE>(__fadd_rn(hs, ls));
-          const float eh2 = grid_round<kGridE>(__fadd_rn(hs2, ls2));
-          Eh[s][p][r] = make_float2(eh, eh2);
-          El[s][p][r] = make_float2(__fadd_rn(__fsub_rn(hs, eh), ls), __fadd_rn(__fsub_rn(hs2, eh2), ls2));
+          // full = (Nh + Nl) 2^-e; hi = grid(full); lo = (Nh 2^-e - hi) + Nl 2^-e, where
+          // Nh 2^-e - hi is exact (both on grids whose difference fits in 24 bits)
+          const float fx = __fmul_rn(V[s][p][r].x, sc), fy = __fmul_rn(V[s][p][r].y, sc);
+          const float hx = grid_round<kGridE>(fx), hy = grid_round<kGridE>(fy);
+          Eh[s][p][r] = make_float2(hx, hy);
+          El[s][p][r] = make_float2(__fmaf_rn(Nl[s][p][r].x, sc, __fmaf_rn(Nh[s][p][r].x, sc, -hx)),
+                                    __fmaf_rn(Nl[s][p][r].y, sc, __fmaf_rn(Nh[s][p][r].y, sc, -hy)));
+          Ef[s][p][r] = make_float2(fx, fy);
         }
     L += e;
   }
@@ -474,22 +475,36 @@ template <int CHI, int PREC>
 struct TileCfg {
   using Rec = Record<CHI, PREC>;
   static constexpr int TI = 16;                               // TI x TI pairs, one per thread
+  static constexpr int kThreads = TI * TI;
+  static constexpr int kWarps = kThreads / 32;
   static constexpr int S = (Rec::kBytes >= 1024) ? 1 : (1024 / Rec::kBytes);  // sites per chunk
+  static constexpr int kStages = 3;                           // chunks in flight
   static constexpr int SLOT = S * Rec::kBytes + 16;           // +16 B: spreads points over banks
   static constexpr int STAGE = 2 * TI * SLOT;
   static constexpr int kOutBytes = TI * (TI + 1) * 16;
-  static constexpr int kSmem = 2 * STAGE + kOutBytes + 64;
+  static constexpr int kCtlBytes = 128;                       // mbarriers, counters, flags
+  static constexpr int kSmem = kStages * STAGE + kOutBytes + kCtlBytes;
+  static constexpr int kMinBlocks = (CHI >= 8) ? 1 : 2;      // CTAs per SM the registers must allow
 };
 
+// One CTA = one TI x TI tile of pairs.  Site records stream through a ring of
+// kStages shared-memory stages.  Stage refill needs no CTA-wide barrier: each
+// warp, after computing a chunk, counts itself out on the stage's counter, and
+// the warp that completes the count issues the bulk copies of the chunk kStages
+// ahead into that stage.  Warps therefore only wait for data (the stage's
+// mbarrier), never for each other inside the site loop.
 template <int CHI, int PREC>
-__global__ void __launch_bounds__(256) pair_tile_kernel(TileArgs args) {
+__global__ void __launch_bounds__(256, (TileCfg<CHI, PREC>::kMinBlocks)) pair_tile_kernel(TileArgs args) {
   using Cfg = TileCfg<CHI, PREC>;
   using Rec = Record<CHI, PREC>;
-  constexpr int TI = Cfg::TI, S = Cfg::S, SLOT = Cfg::SLOT, STAGE = Cfg::STAGE;
+  constexpr int TI = Cfg::TI, S = Cfg::S, SLOT = Cfg::SLOT, STAGE = Cfg::STAGE, NST = Cfg::kStages;
   extern __shared__ __align__(128) uint8_t smem[];
-  double* outK = reinterpret_cast<double*>(smem + 2 * STAGE);
+  double* outK = reinterpret_cast<double*>(smem + NST * STAGE);
   double* outL = outK + TI * (TI + 1);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * STAGE + Cfg::kOutBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NST * STAGE + Cfg::kOutBytes);
+  int* done = reinterpret_cast<int*>(bars + NST);       // per-stage count of warps finished
+  volatile int* abort_flag = done + NST;                 // set by a warp whose wait timed out
+  int* issued = done + NST + 1;                          // chunks issued so far
 
   const int64_t b = args.tile_begin + blockIdx.x;
   int64_t ti, tj;
@@ -504,6 +519,7 @@ __global__ void __launch_bounds__(256) pair_tile_kernel(TileArgs args) {
   const int nj = (int)((args.nB - j0) < TI ? (args.nB - j0) : TI);
   const int n = args.n;
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
   const int ty = tid / TI, tx = tid % TI;
   const bool diag_tile = args.symmetric && ti == tj;
   const bool valid = ty < ni && tx < nj && (!diag_tile || ty <= tx);
@@ -511,14 +527,8 @@ __global__ void __launch_bounds__(256) pair_tile_kernel(TileArgs args) {
   const int slotB = TI + min(tx, nj - 1);
   const int nchunks = (n + S - 1) / S;
 
-  if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-
-  auto issue = [&](int ch, int st) {
+  auto issue = [&](int ch) {
+    const int st = ch % NST;
     const int k0 = ch * S;
     const int ns = min(S, n - k0);
     const uint32_t bytes = (uint32_t)(ns * Rec::kBytes);
@@ -528,23 +538,39 @@ __global__ void __launch_bounds__(256) pair_tile_kernel(TileArgs args) {
       bulk_g2s(base + p * SLOT, args.mpsA + ((i0 + p) * (int64_t)n + k0) * Rec::kBytes, bytes, &bars[st]);
     for (int p = 0; p < nj; ++p)
       bulk_g2s(base + (TI + p) * SLOT, args.mpsB + ((j0 + p) * (int64_t)n + k0) * Rec::kBytes, bytes, &bars[st]);
+    *issued = ch + 1;
   };
 
   if (tid == 0) {
-    issue(0, 0);
-    if (nchunks > 1) issue(1, 1);
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&bars[s], 1);
+      done[s] = 0;
+    }
+    *abort_flag = 0;
+    *issued = 0;
+    fence_mbar_init();
+    for (int ch = 0; ch < min(NST, nchunks); ++ch) issue(ch);
   }
+  __syncthreads();
 
   Engine<CHI, PREC> eng;
   eng.init();
-  int failed_chunk = -1;
   for (int ch = 0; ch < nchunks; ++ch) {
-    const int st = ch & 1;
-    const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((ch >> 1) & 1), kWaitLimitNs);
-    if (__syncthreads_or(!ok)) {
-      failed_chunk = ch;
+    const int st = ch % NST;
+    const uint32_t parity = (uint32_t)((ch / NST) & 1);
+    // bounded wait for the chunk; give up early if another warp already timed out
+    bool ok = mbar_try_wait(&bars[st], parity);
+    if (!ok) {
+      const uint64_t t0 = global_ns();
+      while (!(ok = mbar_try_wait(&bars[st], parity))) {
+        if (*abort_flag || global_ns() - t0 > kWaitLimitNs) break;
+      }
+    }
+    if (!ok) {
+      *abort_flag = 1;
       break;
     }
+    __syncwarp();
     const uint8_t* base = smem + st * STAGE;
     const int k0 = ch * S;
     const int ns = min(S, n - k0);
@@ -558,17 +584,31 @@ __global__ void __launch_bounds__(256) pair_tile_kernel(TileArgs args) {
           eng.renorm();
       }
     }
-    __syncthreads();
-    if (tid == 0 && ch + 2 < nchunks) issue(ch + 2, st);
+    __syncwarp();
+    if (lane == 0) {
+      // all shared-memory reads of this warp for the stage are complete (their
+      // values were consumed above); count the warp out and, if last, refill
+      __threadfence_block();
+      const int prev = atomicAdd(&done[st], 1);
+      if (prev == Cfg::kWarps - 1) {
+        done[st] = 0;
+        if (ch + NST < nchunks) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(ch + NST);
+        }
+      }
+    }
   }
+  __syncthreads();
 
-  if (failed_chunk >= 0) {
+  if (*abort_flag) {
     // A copy never completed: record it, wait (bounded) for the copies this CTA
-    // still has in flight, and leave without writing results.
+    // may still have in flight, and leave without writing results.
     if (tid == 0) {
       atomicCAS(&g_pair_status, 0, (int32_t)QSVM_ERR_TIMEOUT);
-      for (int ch = failed_chunk; ch < min(failed_chunk + 2, nchunks); ++ch)
-        mbar_wait_bounded(&bars[ch & 1], (uint32_t)((ch >> 1) & 1), kDrainLimitNs);
+      const int last = *issued;
+      for (int ch = max(0, last - NST); ch < last; ++ch)
+        mbar_wait_bounded(&bars[ch % NST], (uint32_t)((ch / NST) & 1), kDrainLimitNs);
     }
     return;
   }
