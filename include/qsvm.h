@@ -139,6 +139,64 @@ int32_t qsvm_kernel_gram_tiles(const void* mps, int64_t n_points, int32_t n_qubi
                                int32_t precision, int64_t tile_begin, int64_t tile_end, double* K, int64_t ldk,
                                double* logK, int64_t ldl, void* stream);
 
+/* ---- many Gram jobs in one persistent launch -------------------------------
+ * Sec. 4.1 reuses one contraction path across all pairs and runs contractions
+ * concurrently; here jobs of uneven qubit count and point count share one
+ * persistent kernel: every CTA pulls the next pair tile from a device work
+ * queue (jobs ordered by qubit count, largest first) until it is empty.
+ * All jobs of one call share reps and precision. */
+typedef struct qsvm_job {
+  const void* mps;    /* device MPS of the job's points (qsvm_build_mps)            */
+  int64_t n_points;
+  int32_t n_qubits;   /* >= 2                                                      */
+  int32_t reserved;   /* must be 0                                                 */
+  double* K;          /* device, n_points x n_points, row-major, leading dim ldk    */
+  int64_t ldk;
+  double* logK;       /* device or NULL                                            */
+  int64_t ldl;
+} qsvm_job;
+
+/* Device scratch the batch needs: the job table and the work-queue head. */
+size_t qsvm_batch_workspace_bytes(int32_t n_jobs);
+
+/* qsvm_kernel_batch -- every job's symmetric Gram (as qsvm_kernel_gram) in one
+ * persistent launch.  jobs is a HOST array; ws is device scratch of at least
+ * qsvm_batch_workspace_bytes(n_jobs) bytes (256-byte aligned) that must not be
+ * used by anything else until the launch has finished on `stream`.  The job table
+ * is copied into ws on `stream`.  Errors: QSVM_ERR_ARG, QSVM_ERR_CHI,
+ * QSVM_ERR_WORKSPACE, QSVM_ERR_CUDA. */
+int32_t qsvm_kernel_batch(const qsvm_job* jobs, int32_t n_jobs, int32_t reps, int32_t precision, void* ws,
+                          size_t ws_bytes, void* stream);
+
+/* A batch plan records the queue reset and the persistent launch in a CUDA graph
+ * once (the job table is uploaded at creation) and replays it with one call.
+ * The plan keeps using ws and the jobs' buffers until it is destroyed. */
+typedef struct qsvm_batch_plan qsvm_batch_plan;
+int32_t qsvm_batch_plan_create(const qsvm_job* jobs, int32_t n_jobs, int32_t reps, int32_t precision, void* ws,
+                               size_t ws_bytes, qsvm_batch_plan** plan_out);
+int32_t qsvm_batch_plan_launch(qsvm_batch_plan* plan, void* stream);
+int32_t qsvm_batch_plan_destroy(qsvm_batch_plan* plan);
+
+/* ---- pipeline configurations and the autotuner ----------------------------
+ * The pair kernels stream site records through shared memory in chunks; a
+ * configuration fixes the bytes per point and chunk and the stages in flight.
+ * Results are bit-identical for every configuration (the arithmetic and its
+ * order do not depend on it); only speed differs.  The selection is per
+ * (reps, precision), process-wide, and used by every later launch. */
+int32_t qsvm_num_configs(void);
+/* sites per chunk and stages of configuration `index` for (reps, precision) */
+int32_t qsvm_config_info(int32_t index, int32_t reps, int32_t precision, int32_t* sites_per_chunk,
+                         int32_t* stages);
+int32_t qsvm_set_config(int32_t reps, int32_t precision, int32_t index); /* index -1: default */
+int32_t qsvm_get_config(int32_t reps, int32_t precision);
+/* qsvm_autotune -- times the Gram of `mps` (n_points, n_qubits) under every
+ * configuration with CUDA events on `stream` (writing K as scratch), selects the
+ * fastest for (reps, precision) and returns its index in *best_out; ms_out
+ * (nullable, qsvm_num_configs() floats) gets each time (negative: not runnable).
+ * Synchronises `stream`. */
+int32_t qsvm_autotune(const void* mps, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
+                      double* K, int64_t ldk, void* stream, int32_t* best_out, float* ms_out);
+
 /* ---- diagnostics --------------------------------------------------------- */
 /* Reads (and, if clear != 0, resets) the device status words written by this
  * library's kernels on the current device: QSVM_OK or QSVM_ERR_TIMEOUT.

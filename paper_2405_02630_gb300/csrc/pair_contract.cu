@@ -5,18 +5,43 @@
 
 namespace qsvm {
 
+// Candidate pipeline shapes the autotuner chooses from: bytes of site records per
+// point and chunk, and stages in flight.  Index 1 is the default.
+struct PipeShape {
+  int chunk_bytes;
+  int stages;
+};
+static const PipeShape kShapes[] = {{512, 4}, {1024, 3}, {512, 3}, {1024, 2}, {1024, 4}, {2048, 2}, {2048, 3}, {512, 2}};
+constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+constexpr int kDefaultShape = 1;
+
+int num_pipe_shapes() { return kNumShapes; }
+
+PipeCfg make_pipe(int chi, int prec, int shape) {
+  if (shape < 0 || shape >= kNumShapes) shape = kDefaultShape;
+  const int rec = (int)record_bytes(chi, prec);
+  PipeCfg pc;
+  pc.S = kShapes[shape].chunk_bytes >= rec ? kShapes[shape].chunk_bytes / rec : 1;
+  pc.stages = kShapes[shape].stages;
+  pc.slot_bytes = pc.S * rec + 16;
+  pc.stage_bytes = 2 * kTI * pc.slot_bytes;
+  return pc;
+}
+
+int pipe_smem(const PipeCfg& pc) { return pipe_smem_bytes(pc); }
+
 template <int CHI, int PREC>
-static cudaError_t launch_pair_t(const TileArgs& a, int64_t ntiles, cudaStream_t st) {
-  using Cfg = TileCfg<CHI, PREC>;
+static cudaError_t launch_pair_t(const TileArgs& a, int64_t ntiles, const PipeCfg& pc, cudaStream_t st) {
   auto kern = pair_tile_kernel<CHI, PREC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+  const int smem = pipe_smem_bytes(pc);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int64_t done = 0;
   while (done < ntiles) {
     const int64_t cnt = (ntiles - done) < (int64_t)INT_MAX ? (ntiles - done) : (int64_t)INT_MAX;
     TileArgs b = a;
     b.tile_begin = a.tile_begin + done;
-    kern<<<(unsigned)cnt, Cfg::TI * Cfg::TI, Cfg::kSmem, st>>>(b);
+    kern<<<(unsigned)cnt, kTileThreads, smem, st>>>(b, pc);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     done += cnt;
@@ -24,27 +49,87 @@ static cudaError_t launch_pair_t(const TileArgs& a, int64_t ntiles, cudaStream_t
   return cudaSuccess;
 }
 
+// Sets the kernel's shared-memory attribute and sizes its grid (SMs x resident
+// CTAs per SM, at most one CTA per tile).  Kept out of the launch so a launch can
+// be recorded in a CUDA graph without attribute or occupancy calls inside it.
+template <int CHI, int PREC>
+static cudaError_t prepare_persistent_t(const PipeCfg& pc, int64_t total_tiles, int* grid_out) {
+  auto kern = pair_persistent_kernel<CHI, PREC>;
+  const int smem = pipe_smem_bytes(pc);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > total_tiles) grid = total_tiles;
+  *grid_out = (int)(grid < 1 ? 1 : grid);
+  return cudaSuccess;
+}
+
+template <int CHI, int PREC>
+static cudaError_t launch_persistent_t(const BatchArgs& a, const PipeCfg& pc, int grid, cudaStream_t st) {
+  pair_persistent_kernel<CHI, PREC><<<(unsigned)grid, kTileThreads, pipe_smem_bytes(pc), st>>>(a, pc);
+  return cudaGetLastError();
+}
+
 template <int CHI>
-static cudaError_t launch_pair_c(int prec, const TileArgs& a, int64_t ntiles, cudaStream_t st) {
+static cudaError_t launch_pair_c(int prec, const TileArgs& a, int64_t ntiles, const PipeCfg& pc, cudaStream_t st) {
   switch (prec) {
-    case QSVM_FP64: return launch_pair_t<CHI, QSVM_FP64>(a, ntiles, st);
-    case QSVM_FP32: return launch_pair_t<CHI, QSVM_FP32>(a, ntiles, st);
-    default: return launch_pair_t<CHI, QSVM_FP32_SPLIT>(a, ntiles, st);
+    case QSVM_FP64: return launch_pair_t<CHI, QSVM_FP64>(a, ntiles, pc, st);
+    case QSVM_FP32: return launch_pair_t<CHI, QSVM_FP32>(a, ntiles, pc, st);
+    default: return launch_pair_t<CHI, QSVM_FP32_SPLIT>(a, ntiles, pc, st);
   }
 }
 
-cudaError_t launch_pair(int chi, int prec, const TileArgs& a, int64_t ntiles, cudaStream_t st) {
+template <int CHI>
+static cudaError_t prepare_persistent_c(int prec, const PipeCfg& pc, int64_t total, int* g) {
+  switch (prec) {
+    case QSVM_FP64: return prepare_persistent_t<CHI, QSVM_FP64>(pc, total, g);
+    case QSVM_FP32: return prepare_persistent_t<CHI, QSVM_FP32>(pc, total, g);
+    default: return prepare_persistent_t<CHI, QSVM_FP32_SPLIT>(pc, total, g);
+  }
+}
+
+template <int CHI>
+static cudaError_t launch_persistent_c(int prec, const BatchArgs& a, const PipeCfg& pc, int grid, cudaStream_t st) {
+  switch (prec) {
+    case QSVM_FP64: return launch_persistent_t<CHI, QSVM_FP64>(a, pc, grid, st);
+    case QSVM_FP32: return launch_persistent_t<CHI, QSVM_FP32>(a, pc, grid, st);
+    default: return launch_persistent_t<CHI, QSVM_FP32_SPLIT>(a, pc, grid, st);
+  }
+}
+
+cudaError_t launch_pair(int chi, int prec, const TileArgs& a, int64_t ntiles, const PipeCfg& pc, cudaStream_t st) {
   switch (chi) {
-    case 2: return launch_pair_c<2>(prec, a, ntiles, st);
-    case 4: return launch_pair_c<4>(prec, a, ntiles, st);
-    default: return launch_pair_c<8>(prec, a, ntiles, st);
+    case 2: return launch_pair_c<2>(prec, a, ntiles, pc, st);
+    case 4: return launch_pair_c<4>(prec, a, ntiles, pc, st);
+    default: return launch_pair_c<8>(prec, a, ntiles, pc, st);
+  }
+}
+
+cudaError_t prepare_persistent(int chi, int prec, const PipeCfg& pc, int64_t total_tiles, int* grid_out) {
+  switch (chi) {
+    case 2: return prepare_persistent_c<2>(prec, pc, total_tiles, grid_out);
+    case 4: return prepare_persistent_c<4>(prec, pc, total_tiles, grid_out);
+    default: return prepare_persistent_c<8>(prec, pc, total_tiles, grid_out);
+  }
+}
+
+cudaError_t launch_persistent(int chi, int prec, const BatchArgs& a, const PipeCfg& pc, int grid, cudaStream_t st) {
+  switch (chi) {
+    case 2: return launch_persistent_c<2>(prec, a, pc, grid, st);
+    case 4: return launch_persistent_c<4>(prec, a, pc, grid, st);
+    default: return launch_persistent_c<8>(prec, a, pc, grid, st);
   }
 }
 
 int pair_tile_dim(int chi, int prec) {
   (void)chi;
   (void)prec;
-  return TileCfg<4, QSVM_FP64>::TI;
+  return kTI;
 }
 
 cudaError_t pair_status(cudaStream_t st, int clear, int32_t* out) {

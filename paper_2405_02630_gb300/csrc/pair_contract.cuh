@@ -27,8 +27,17 @@
 namespace qsvm {
 
 // ---------------------------------------------------------- loads ---------
+// Site records are addressed by 32-bit shared-window offsets and read through a
+// __shared__-derived pointer, so the compiler emits LDS and can schedule them.
+extern __shared__ __align__(128) uint8_t qsvm_dyn_smem[];
+
+__device__ __forceinline__ const uint8_t* sptr(uint32_t a) {
+  return qsvm_dyn_smem + (a - static_cast<uint32_t>(__cvta_generic_to_shared(qsvm_dyn_smem)));
+}
+
 template <int H>
-__device__ __forceinline__ void load_block_f(const uint8_t* p, float2 (&d)[H][H]) {
+__device__ __forceinline__ void load_block_f(uint32_t a, float2 (&d)[H][H]) {
+  const uint8_t* p = sptr(a);
   if constexpr ((H * H) % 2 == 0) {
     const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
@@ -45,8 +54,8 @@ __device__ __forceinline__ void load_block_f(const uint8_t* p, float2 (&d)[H][H]
 }
 
 template <int H>
-__device__ __forceinline__ void load_block_d(const uint8_t* p, double2 (&d)[H][H]) {
-  const double2* q = reinterpret_cast<const double2*>(p);
+__device__ __forceinline__ void load_block_d(uint32_t a, double2 (&d)[H][H]) {
+  const double2* q = reinterpret_cast<const double2*>(sptr(a));
 #pragma unroll
   for (int e = 0; e < H * H; ++e) d[e / H][e % H] = q[e];
 }
@@ -75,7 +84,7 @@ struct Engine<CHI, QSVM_FP64> {
     L = 0;
   }
 
-  __device__ __forceinline__ void site(const uint8_t* ra, const uint8_t* rb) {
+  __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     double2 N[2][H][H];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -181,7 +190,7 @@ struct Engine<CHI, QSVM_FP32> {
     L = 0;
   }
 
-  __device__ __forceinline__ void site(const uint8_t* ra, const uint8_t* rb) {
+  __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     float2 N[2][H][H];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -316,7 +325,7 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
     L = 0;
   }
 
-  __device__ __forceinline__ void site(const uint8_t* ra, const uint8_t* rb) {
+  __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     float2 Nh[2][H][H], Nl[2][H][H];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -328,8 +337,8 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
     for (int s = 0; s < 2; ++s) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const uint8_t* pa = ra + (2 * c + s) * Rec::kBlockBytes;
-        const uint8_t* pb = rb + (2 * c + s) * Rec::kBlockBytes;
+        const uint32_t pa = ra + (2 * c + s) * Rec::kBlockBytes;
+        const uint32_t pb = rb + (2 * c + s) * Rec::kBlockBytes;
         float2 ah[H][H], al[H][H], bh[H][H], bl[H][H];
         load_block_f<H>(pa, ah);
         load_block_f<H>(pa + H * H * 8, al);
@@ -471,112 +480,118 @@ __device__ __forceinline__ void tri_decode(int64_t b, int64_t T, int64_t& ti, in
   tj = r + (b - (r * T - r * (r - 1) / 2));
 }
 
+constexpr int kTI = 16;               // a tile is kTI x kTI pairs, one per thread
+constexpr int kTileThreads = kTI * kTI;
+constexpr int kTileWarps = kTileThreads / 32;
+constexpr int kMaxStages = 4;
+constexpr int kOutBytes = kTI * (kTI + 1) * 16;
+constexpr int kCtlBytes = 128;
+
 template <int CHI, int PREC>
-struct TileCfg {
-  using Rec = Record<CHI, PREC>;
-  static constexpr int TI = 16;                               // TI x TI pairs, one per thread
-  static constexpr int kThreads = TI * TI;
-  static constexpr int kWarps = kThreads / 32;
-  static constexpr int S = (Rec::kBytes >= 1024) ? 1 : (1024 / Rec::kBytes);  // sites per chunk
-  static constexpr int kStages = 3;                           // chunks in flight
-  static constexpr int SLOT = S * Rec::kBytes + 16;           // +16 B: spreads points over banks
-  static constexpr int STAGE = 2 * TI * SLOT;
-  static constexpr int kOutBytes = TI * (TI + 1) * 16;
-  static constexpr int kCtlBytes = 128;                       // mbarriers, counters, flags
-  static constexpr int kSmem = kStages * STAGE + kOutBytes + kCtlBytes;
-  static constexpr int kMinBlocks = (CHI >= 8) ? 1 : 2;      // CTAs per SM the registers must allow
+__host__ __device__ constexpr int min_blocks_per_sm() {
+  return (CHI >= 8) ? 1 : ((PREC == QSVM_FP32) ? 3 : 2);
+}
+
+// Shared-memory control block at the end of the dynamic allocation.
+struct TileCtl {
+  uint64_t bars[kMaxStages];  // one "full" mbarrier per stage
+  int done[kMaxStages];       // warps finished with the stage's current chunk
+  int abort_flag;             // a wait timed out somewhere in the CTA
+  int issued;                 // chunks issued (global count)
+  long long next_tile;        // persistent kernel: tile fetched for the CTA
+};
+static_assert(sizeof(TileCtl) <= kCtlBytes, "control block");
+
+__host__ __device__ inline int pipe_smem_bytes(const PipeCfg& pc) { return pc.stages * pc.stage_bytes + kOutBytes + kCtlBytes; }
+
+// What one tile needs to know.
+struct TileWork {
+  const uint8_t* mpsA;
+  const uint8_t* mpsB;
+  int64_t nA, nB;
+  int64_t ti, tj;
+  int n;
+  int symmetric;
+  double* K;
+  int64_t ldk;
+  double* logK;
+  int64_t ldl;
 };
 
-// One CTA = one TI x TI tile of pairs.  Site records stream through a ring of
-// kStages shared-memory stages.  Stage refill needs no CTA-wide barrier: each
-// warp, after computing a chunk, counts itself out on the stage's counter, and
-// the warp that completes the count issues the bulk copies of the chunk kStages
-// ahead into that stage.  Warps therefore only wait for data (the stage's
-// mbarrier), never for each other inside the site loop.
+// Contract one TI x TI tile of pairs.  Site records stream through a ring of
+// pc.stages shared-memory stages of pc.S sites each.  Stage refill needs no
+// CTA-wide barrier: each warp, after computing a chunk, counts itself out on the
+// stage's counter, and the warp that completes the count issues the bulk copies
+// of the chunk pc.stages ahead into that stage; warps only wait for data.
+// gchunk is the CTA's running chunk count (stage and mbarrier parity continue
+// across the tiles a persistent CTA processes).  Returns false after a timeout.
 template <int CHI, int PREC>
-__global__ void __launch_bounds__(256, (TileCfg<CHI, PREC>::kMinBlocks)) pair_tile_kernel(TileArgs args) {
-  using Cfg = TileCfg<CHI, PREC>;
+__device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, uint8_t* smem, TileCtl* ctl,
+                                         int& gchunk) {
   using Rec = Record<CHI, PREC>;
-  constexpr int TI = Cfg::TI, S = Cfg::S, SLOT = Cfg::SLOT, STAGE = Cfg::STAGE, NST = Cfg::kStages;
-  extern __shared__ __align__(128) uint8_t smem[];
+  constexpr int TI = kTI;
+  const int S = pc.S, NST = pc.stages, SLOT = pc.slot_bytes, STAGE = pc.stage_bytes;
   double* outK = reinterpret_cast<double*>(smem + NST * STAGE);
   double* outL = outK + TI * (TI + 1);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NST * STAGE + Cfg::kOutBytes);
-  int* done = reinterpret_cast<int*>(bars + NST);       // per-stage count of warps finished
-  volatile int* abort_flag = done + NST;                 // set by a warp whose wait timed out
-  int* issued = done + NST + 1;                          // chunks issued so far
 
-  const int64_t b = args.tile_begin + blockIdx.x;
-  int64_t ti, tj;
-  if (args.symmetric) {
-    tri_decode(b, args.tiles_j, ti, tj);
-  } else {
-    ti = b / args.tiles_j;
-    tj = b - ti * args.tiles_j;
-  }
-  const int64_t i0 = ti * TI, j0 = tj * TI;
-  const int ni = (int)((args.nA - i0) < TI ? (args.nA - i0) : TI);
-  const int nj = (int)((args.nB - j0) < TI ? (args.nB - j0) : TI);
-  const int n = args.n;
+  const int64_t i0 = w.ti * TI, j0 = w.tj * TI;
+  const int ni = (int)((w.nA - i0) < TI ? (w.nA - i0) : TI);
+  const int nj = (int)((w.nB - j0) < TI ? (w.nB - j0) : TI);
+  const int n = w.n;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int ty = tid / TI, tx = tid % TI;
-  const bool diag_tile = args.symmetric && ti == tj;
+  const bool diag_tile = w.symmetric && w.ti == w.tj;
   const bool valid = ty < ni && tx < nj && (!diag_tile || ty <= tx);
   const int slotA = min(ty, ni - 1);
   const int slotB = TI + min(tx, nj - 1);
   const int nchunks = (n + S - 1) / S;
+  const int g0 = gchunk;
 
   auto issue = [&](int ch) {
-    const int st = ch % NST;
+    const int g = g0 + ch;
+    const int st = g % NST;
     const int k0 = ch * S;
     const int ns = min(S, n - k0);
     const uint32_t bytes = (uint32_t)(ns * Rec::kBytes);
-    mbar_arrive_expect_tx(&bars[st], bytes * (uint32_t)(ni + nj));
+    mbar_arrive_expect_tx(&ctl->bars[st], bytes * (uint32_t)(ni + nj));
     uint8_t* base = smem + st * STAGE;
     for (int p = 0; p < ni; ++p)
-      bulk_g2s(base + p * SLOT, args.mpsA + ((i0 + p) * (int64_t)n + k0) * Rec::kBytes, bytes, &bars[st]);
+      bulk_g2s(base + p * SLOT, w.mpsA + ((i0 + p) * (int64_t)n + k0) * Rec::kBytes, bytes, &ctl->bars[st]);
     for (int p = 0; p < nj; ++p)
-      bulk_g2s(base + (TI + p) * SLOT, args.mpsB + ((j0 + p) * (int64_t)n + k0) * Rec::kBytes, bytes, &bars[st]);
-    *issued = ch + 1;
+      bulk_g2s(base + (TI + p) * SLOT, w.mpsB + ((j0 + p) * (int64_t)n + k0) * Rec::kBytes, bytes, &ctl->bars[st]);
+    ctl->issued = g + 1;
   };
 
-  if (tid == 0) {
-    for (int s = 0; s < NST; ++s) {
-      mbar_init(&bars[s], 1);
-      done[s] = 0;
-    }
-    *abort_flag = 0;
-    *issued = 0;
-    fence_mbar_init();
+  if (tid == 0)
     for (int ch = 0; ch < min(NST, nchunks); ++ch) issue(ch);
-  }
   __syncthreads();
 
   Engine<CHI, PREC> eng;
   eng.init();
   for (int ch = 0; ch < nchunks; ++ch) {
-    const int st = ch % NST;
-    const uint32_t parity = (uint32_t)((ch / NST) & 1);
+    const int g = g0 + ch;
+    const int st = g % NST;
+    const uint32_t parity = (uint32_t)((g / NST) & 1);
     // bounded wait for the chunk; give up early if another warp already timed out
-    bool ok = mbar_try_wait(&bars[st], parity);
+    bool ok = mbar_try_wait(&ctl->bars[st], parity);
     if (!ok) {
       const uint64_t t0 = global_ns();
-      while (!(ok = mbar_try_wait(&bars[st], parity))) {
-        if (*abort_flag || global_ns() - t0 > kWaitLimitNs) break;
+      while (!(ok = mbar_try_wait(&ctl->bars[st], parity))) {
+        if (*(volatile int*)&ctl->abort_flag || global_ns() - t0 > kWaitLimitNs) break;
       }
     }
     if (!ok) {
-      *abort_flag = 1;
+      *(volatile int*)&ctl->abort_flag = 1;
       break;
     }
     __syncwarp();
-    const uint8_t* base = smem + st * STAGE;
+    const uint32_t base = smem_u32(smem) + st * STAGE;
     const int k0 = ch * S;
     const int ns = min(S, n - k0);
     if (valid) {
-      const uint8_t* pa = base + slotA * SLOT;
-      const uint8_t* pb = base + slotB * SLOT;
+      const uint32_t pa = base + slotA * SLOT;
+      const uint32_t pb = base + slotB * SLOT;
 #pragma unroll 1
       for (int s = 0; s < ns; ++s) {
         eng.site(pa + s * Rec::kBytes, pb + s * Rec::kBytes);
@@ -589,9 +604,9 @@ __global__ void __launch_bounds__(256, (TileCfg<CHI, PREC>::kMinBlocks)) pair_ti
       // all shared-memory reads of this warp for the stage are complete (their
       // values were consumed above); count the warp out and, if last, refill
       __threadfence_block();
-      const int prev = atomicAdd(&done[st], 1);
-      if (prev == Cfg::kWarps - 1) {
-        done[st] = 0;
+      const int prev = atomicAdd(&ctl->done[st], 1);
+      if (prev == kTileWarps - 1) {
+        ctl->done[st] = 0;
         if (ch + NST < nchunks) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           issue(ch + NST);
@@ -600,17 +615,18 @@ __global__ void __launch_bounds__(256, (TileCfg<CHI, PREC>::kMinBlocks)) pair_ti
     }
   }
   __syncthreads();
+  gchunk = g0 + nchunks;
 
-  if (*abort_flag) {
+  if (ctl->abort_flag) {
     // A copy never completed: record it, wait (bounded) for the copies this CTA
-    // may still have in flight, and leave without writing results.
+    // may still have in flight, and stop without writing results.
     if (tid == 0) {
       atomicCAS(&g_pair_status, 0, (int32_t)QSVM_ERR_TIMEOUT);
-      const int last = *issued;
-      for (int ch = max(0, last - NST); ch < last; ++ch)
-        mbar_wait_bounded(&bars[ch % NST], (uint32_t)((ch / NST) & 1), kDrainLimitNs);
+      const int last = ctl->issued;
+      for (int g = max(0, last - NST); g < last; ++g)
+        mbar_wait_bounded(&ctl->bars[g % NST], (uint32_t)((g / NST) & 1), kDrainLimitNs);
     }
-    return;
+    return false;
   }
 
   double kval = 0.0, lval = -INFINITY;
@@ -623,10 +639,10 @@ __global__ void __launch_bounds__(256, (TileCfg<CHI, PREC>::kMinBlocks)) pair_ti
       kval = ldexp(a2, 2 * eng.L);
       lval = log(a2) + (double)(2 * eng.L) * 0.69314718055994530942;
     }
-    args.K[(i0 + ty) * args.ldk + (j0 + tx)] = kval;
-    if (args.logK) args.logK[(i0 + ty) * args.ldl + (j0 + tx)] = lval;
+    w.K[(i0 + ty) * w.ldk + (j0 + tx)] = kval;
+    if (w.logK) w.logK[(i0 + ty) * w.ldl + (j0 + tx)] = lval;
   }
-  if (args.symmetric) {
+  if (w.symmetric) {
     // mirror K[j][i] = K[i][j] bit-exactly, through shared memory so that the
     // transposed rows are written contiguously
     outK[ty * (TI + 1) + tx] = kval;
@@ -635,9 +651,95 @@ __global__ void __launch_bounds__(256, (TileCfg<CHI, PREC>::kMinBlocks)) pair_ti
     // this thread writes row j0+ty, column i0+tx: the value of pair (i0+tx, j0+ty)
     const bool src = tx < ni && ty < nj && (!diag_tile || tx < ty);
     if (src) {
-      args.K[(j0 + ty) * args.ldk + (i0 + tx)] = outK[tx * (TI + 1) + ty];
-      if (args.logK) args.logK[(j0 + ty) * args.ldl + (i0 + tx)] = outL[tx * (TI + 1) + ty];
+      w.K[(j0 + ty) * w.ldk + (i0 + tx)] = outK[tx * (TI + 1) + ty];
+      if (w.logK) w.logK[(j0 + ty) * w.ldl + (i0 + tx)] = outL[tx * (TI + 1) + ty];
     }
+    __syncthreads();  // outK is reused by the next tile of a persistent CTA
+  }
+  return true;
+}
+
+__device__ __forceinline__ TileCtl* tile_ctl(uint8_t* smem, const PipeCfg& pc) {
+  return reinterpret_cast<TileCtl*>(smem + pc.stages * pc.stage_bytes + kOutBytes);
+}
+
+__device__ __forceinline__ void tile_ctl_init(TileCtl* ctl, const PipeCfg& pc) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < pc.stages; ++s) {
+      mbar_init(&ctl->bars[s], 1);
+      ctl->done[s] = 0;
+    }
+    ctl->abort_flag = 0;
+    ctl->issued = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+}
+
+// One CTA per tile of a launch (grid = number of tiles in [tile_begin, ...)).
+template <int CHI, int PREC>
+__global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>()))
+    pair_tile_kernel(TileArgs args, PipeCfg pc) {
+  uint8_t* smem = qsvm_dyn_smem;
+  TileCtl* ctl = tile_ctl(smem, pc);
+  tile_ctl_init(ctl, pc);
+  const int64_t b = args.tile_begin + blockIdx.x;
+  TileWork w;
+  if (args.symmetric) {
+    tri_decode(b, args.tiles_j, w.ti, w.tj);
+  } else {
+    w.ti = b / args.tiles_j;
+    w.tj = b - w.ti * args.tiles_j;
+  }
+  w.mpsA = args.mpsA;
+  w.mpsB = args.mpsB;
+  w.nA = args.nA;
+  w.nB = args.nB;
+  w.n = args.n;
+  w.symmetric = args.symmetric;
+  w.K = args.K;
+  w.ldk = args.ldk;
+  w.logK = args.logK;
+  w.ldl = args.ldl;
+  int gchunk = 0;
+  run_tile<CHI, PREC>(w, pc, smem, ctl, gchunk);
+}
+
+// Persistent kernel over a queue of Gram tiles from many jobs: every CTA pulls
+// the next tile index from a device counter until the queue is empty.  Jobs are
+// ordered heaviest first by the host; tile t belongs to the job j with
+// prefix[j] <= t < prefix[j + 1].
+template <int CHI, int PREC>
+__global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>()))
+    pair_persistent_kernel(BatchArgs args, PipeCfg pc) {
+  uint8_t* smem = qsvm_dyn_smem;
+  TileCtl* ctl = tile_ctl(smem, pc);
+  tile_ctl_init(ctl, pc);
+  int gchunk = 0;
+  while (true) {
+    if (threadIdx.x == 0) ctl->next_tile = (long long)atomicAdd(args.counter, 1ull);
+    __syncthreads();
+    const int64_t t = (int64_t)ctl->next_tile;
+    __syncthreads();  // next_tile is rewritten on the next iteration
+    if (t >= args.total_tiles) break;
+    int lo = 0, hi = args.n_jobs - 1;  // last job whose prefix <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (args.prefix[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const DevJob& J = args.jobs[lo];
+    TileWork w;
+    tri_decode(t - args.prefix[lo], J.tiles, w.ti, w.tj);
+    w.mpsA = w.mpsB = J.mps;
+    w.nA = w.nB = J.n_points;
+    w.n = J.n_qubits;
+    w.symmetric = 1;
+    w.K = J.K;
+    w.ldk = J.ldk;
+    w.logK = J.logK;
+    w.ldl = J.ldl;
+    if (!run_tile<CHI, PREC>(w, pc, smem, ctl, gchunk)) break;
   }
 }
 

@@ -8,11 +8,19 @@
 
 #include "qsvm_common.cuh"
 
+#include <atomic>
+#include <vector>
+
 namespace qsvm {
 cudaError_t launch_build_mps(const double* X, int64_t N, int n, int reps, int prec, void* mps, cudaStream_t st);
-cudaError_t launch_pair(int chi, int prec, const TileArgs& a, int64_t ntiles, cudaStream_t st);
+cudaError_t launch_pair(int chi, int prec, const TileArgs& a, int64_t ntiles, const PipeCfg& pc, cudaStream_t st);
+cudaError_t prepare_persistent(int chi, int prec, const PipeCfg& pc, int64_t total_tiles, int* grid_out);
+cudaError_t launch_persistent(int chi, int prec, const BatchArgs& a, const PipeCfg& pc, int grid, cudaStream_t st);
 int pair_tile_dim(int chi, int prec);
 cudaError_t pair_status(cudaStream_t st, int clear, int32_t* out);
+int num_pipe_shapes();
+PipeCfg make_pipe(int chi, int prec, int shape);
+int pipe_smem(const PipeCfg& pc);
 }  // namespace qsvm
 
 using namespace qsvm;
@@ -46,6 +54,13 @@ int32_t check_common(int32_t n_qubits, int32_t reps, int32_t precision) {
 }
 
 int64_t tiles_per_side(int64_t n_points, int tdim) { return (n_points + tdim - 1) / tdim; }
+
+// selected pipeline configuration per (reps - 1, precision); -1 = default
+std::atomic<int> g_config[3][3] = {{{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}};
+
+PipeCfg current_pipe(int reps, int prec) { return make_pipe(1 << reps, prec, g_config[reps - 1][prec].load()); }
+
+constexpr int kMaxSmemPerCta = 227 * 1024;
 
 // pairs contracted by upper-triangle tile b of a T x T grid over n_points
 int64_t tile_pairs(int64_t ti, int64_t tj, int64_t n_points, int tdim) {
@@ -84,12 +99,86 @@ int32_t gram_launch(const void* mps, int64_t n_points, int32_t n_qubits, int32_t
   a.ldk = ldk;
   a.logK = logK;
   a.ldl = ldl;
-  cudaError_t e = launch_pair(chi, precision, a, tile_end - tile_begin, static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_pair(chi, precision, a, tile_end - tile_begin, current_pipe(reps, precision),
+                              static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "pair kernel launch");
   return QSVM_OK;
 }
 
+// ---- batch job table -------------------------------------------------------
+constexpr size_t kWsAlign = 256;
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+size_t ws_jobs_offset() { return kWsAlign; }
+size_t ws_prefix_offset(int n_jobs) { return align_up(ws_jobs_offset() + sizeof(DevJob) * (size_t)n_jobs, kWsAlign); }
+size_t ws_total(int n_jobs) { return align_up(ws_prefix_offset(n_jobs) + sizeof(int64_t) * (size_t)(n_jobs + 1), kWsAlign); }
+
+// Host image of the workspace (counter slot, sorted job table, tile prefix).
+struct BatchImage {
+  std::vector<uint8_t> bytes;
+  int64_t total_tiles = 0;
+};
+
+int32_t build_batch_image(const qsvm_job* jobs, int32_t n_jobs, int32_t reps, int32_t precision, const void* ws,
+                          size_t ws_bytes, BatchImage& img) {
+  int32_t rc = check_common(2, reps, precision);
+  if (rc) return rc;
+  if (!jobs || n_jobs < 1) return fail(QSVM_ERR_ARG, "jobs must be a non-empty host array");
+  if (!ws || !aligned(ws, kWsAlign)) return fail(QSVM_ERR_ARG, "ws must be a non-null 256-byte aligned device pointer");
+  if (ws_bytes < ws_total(n_jobs))
+    return fail(QSVM_ERR_WORKSPACE, "ws_bytes=%zu < required %zu", ws_bytes, ws_total(n_jobs));
+  const int tdim = pair_tile_dim(1 << reps, precision);
+  std::vector<int> order((size_t)n_jobs);
+  for (int j = 0; j < n_jobs; ++j) {
+    const qsvm_job& J = jobs[j];
+    if (!J.mps || !aligned(J.mps, 16) || J.n_points < 1 || J.n_qubits < 2 || !J.K || !aligned(J.K, 8) ||
+        J.ldk < J.n_points || (J.logK && (!aligned(J.logK, 8) || J.ldl < J.n_points)) || J.reserved != 0)
+      return fail(QSVM_ERR_ARG, "job %d: invalid pointer, size or leading dimension", j);
+    order[(size_t)j] = j;
+  }
+  // heaviest tiles first: cost per tile grows with the qubit count
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].n_qubits > jobs[b].n_qubits; });
+  img.bytes.assign(ws_total(n_jobs), 0);
+  DevJob* dj = reinterpret_cast<DevJob*>(img.bytes.data() + ws_jobs_offset());
+  int64_t* prefix = reinterpret_cast<int64_t*>(img.bytes.data() + ws_prefix_offset(n_jobs));
+  int64_t acc = 0;
+  for (int k = 0; k < n_jobs; ++k) {
+    const qsvm_job& J = jobs[order[(size_t)k]];
+    const int64_t T = tiles_per_side(J.n_points, tdim);
+    dj[k].mps = static_cast<const uint8_t*>(J.mps);
+    dj[k].n_points = J.n_points;
+    dj[k].tiles = T;
+    dj[k].K = J.K;
+    dj[k].ldk = J.ldk;
+    dj[k].logK = J.logK;
+    dj[k].ldl = J.ldl;
+    dj[k].n_qubits = J.n_qubits;
+    dj[k].pad = 0;
+    prefix[k] = acc;
+    acc += T * (T + 1) / 2;
+  }
+  prefix[n_jobs] = acc;
+  img.total_tiles = acc;
+  return QSVM_OK;
+}
+
+BatchArgs batch_args(void* ws, int32_t n_jobs, int64_t total) {
+  BatchArgs a{};
+  uint8_t* base = static_cast<uint8_t*>(ws);
+  a.counter = reinterpret_cast<unsigned long long*>(base);
+  a.jobs = reinterpret_cast<const DevJob*>(base + ws_jobs_offset());
+  a.prefix = reinterpret_cast<const int64_t*>(base + ws_prefix_offset(n_jobs));
+  a.n_jobs = n_jobs;
+  a.total_tiles = total;
+  return a;
+}
+
 }  // namespace
+
+struct qsvm_batch_plan {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int device = 0;
+};
 
 extern "C" {
 
@@ -200,8 +289,153 @@ int32_t qsvm_kernel_cross(const void* mps_a, int64_t n_a, const void* mps_b, int
   a.ldk = ldk;
   a.logK = logK;
   a.ldl = ldl;
-  cudaError_t e = launch_pair(chi, precision, a, Ta * Tb, static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_pair(chi, precision, a, Ta * Tb, current_pipe(reps, precision), static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "pair kernel launch");
+  return QSVM_OK;
+}
+
+size_t qsvm_batch_workspace_bytes(int32_t n_jobs) { return n_jobs < 1 ? 0 : ws_total(n_jobs); }
+
+int32_t qsvm_kernel_batch(const qsvm_job* jobs, int32_t n_jobs, int32_t reps, int32_t precision, void* ws,
+                          size_t ws_bytes, void* stream) {
+  BatchImage img;
+  int32_t rc = build_batch_image(jobs, n_jobs, reps, precision, ws, ws_bytes, img);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // pageable source: the call returns once the bytes are staged, so img may go
+  cudaError_t e = cudaMemcpyAsync(ws, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batch job table upload");
+  const BatchArgs a = batch_args(ws, n_jobs, img.total_tiles);
+  const PipeCfg pc = current_pipe(reps, precision);
+  int grid = 0;
+  e = prepare_persistent(1 << reps, precision, pc, img.total_tiles, &grid);
+  if (e == cudaSuccess) e = launch_persistent(1 << reps, precision, a, pc, grid, st);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
+  return QSVM_OK;
+}
+
+int32_t qsvm_batch_plan_create(const qsvm_job* jobs, int32_t n_jobs, int32_t reps, int32_t precision, void* ws,
+                               size_t ws_bytes, qsvm_batch_plan** plan_out) {
+  if (!plan_out) return fail(QSVM_ERR_ARG, "plan_out is null");
+  *plan_out = nullptr;
+  BatchImage img;
+  int32_t rc = build_batch_image(jobs, n_jobs, reps, precision, ws, ws_bytes, img);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpy(ws, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "batch job table upload");
+  auto* plan = new qsvm_batch_plan();
+  cudaGetDevice(&plan->device);
+  cudaStream_t cap = nullptr;
+  e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete plan;
+    return cuda_fail(e, "capture stream");
+  }
+  const BatchArgs a = batch_args(ws, n_jobs, img.total_tiles);
+  const PipeCfg pc = current_pipe(reps, precision);
+  int grid = 0;
+  e = prepare_persistent(1 << reps, precision, pc, img.total_tiles, &grid);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), cap);
+    cudaError_t e2 = (e1 == cudaSuccess) ? launch_persistent(1 << reps, precision, a, pc, grid, cap) : e1;
+    e = cudaStreamEndCapture(cap, &plan->graph);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    delete plan;
+    return cuda_fail(e, "batch graph capture");
+  }
+  *plan_out = plan;
+  return QSVM_OK;
+}
+
+int32_t qsvm_batch_plan_launch(qsvm_batch_plan* plan, void* stream) {
+  if (!plan || !plan->exec) return fail(QSVM_ERR_ARG, "null plan");
+  cudaError_t e = cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  return QSVM_OK;
+}
+
+int32_t qsvm_batch_plan_destroy(qsvm_batch_plan* plan) {
+  if (!plan) return QSVM_OK;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  delete plan;
+  return QSVM_OK;
+}
+
+int32_t qsvm_num_configs(void) { return num_pipe_shapes(); }
+
+int32_t qsvm_config_info(int32_t index, int32_t reps, int32_t precision, int32_t* sites_per_chunk, int32_t* stages) {
+  int32_t rc = check_common(2, reps, precision);
+  if (rc) return rc;
+  if (index < 0 || index >= num_pipe_shapes()) return fail(QSVM_ERR_ARG, "config index %d out of range", index);
+  const PipeCfg pc = make_pipe(1 << reps, precision, index);
+  if (sites_per_chunk) *sites_per_chunk = pc.S;
+  if (stages) *stages = pc.stages;
+  return QSVM_OK;
+}
+
+int32_t qsvm_set_config(int32_t reps, int32_t precision, int32_t index) {
+  int32_t rc = check_common(2, reps, precision);
+  if (rc) return rc;
+  if (index < -1 || index >= num_pipe_shapes()) return fail(QSVM_ERR_ARG, "config index %d out of range", index);
+  if (index >= 0 && pipe_smem(make_pipe(1 << reps, precision, index)) > kMaxSmemPerCta)
+    return fail(QSVM_ERR_ARG, "config %d needs more shared memory than a CTA has", index);
+  g_config[reps - 1][precision].store(index);
+  return QSVM_OK;
+}
+
+int32_t qsvm_get_config(int32_t reps, int32_t precision) {
+  if (reps < 1 || reps > 3 || precision < QSVM_FP64 || precision > QSVM_FP32_SPLIT) return -1;
+  return g_config[reps - 1][precision].load();
+}
+
+int32_t qsvm_autotune(const void* mps, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
+                      double* K, int64_t ldk, void* stream, int32_t* best_out, float* ms_out) {
+  int32_t rc = check_common(n_qubits, reps, precision);
+  if (rc) return rc;
+  if (!best_out) return fail(QSVM_ERR_ARG, "best_out is null");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int prev = g_config[reps - 1][precision].load();
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "event create");
+  int best = -1;
+  float best_ms = 0.f;
+  int32_t out = QSVM_OK;
+  for (int c = 0; c < num_pipe_shapes() && out == QSVM_OK; ++c) {
+    float ms = -1.f;
+    if (pipe_smem(make_pipe(1 << reps, precision, c)) <= kMaxSmemPerCta) {
+      g_config[reps - 1][precision].store(c);
+      // one untimed run, then the timed one
+      for (int it = 0; it < 2 && out == QSVM_OK; ++it) {
+        if (it == 1) cudaEventRecord(e0, st);
+        out = qsvm_kernel_gram(mps, n_points, n_qubits, reps, precision, K, ldk, nullptr, 0, stream);
+        if (it == 1) cudaEventRecord(e1, st);
+      }
+      if (out == QSVM_OK) {
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) out = cuda_fail(e, "autotune timing");
+        else cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (out == QSVM_OK && (best < 0 || ms < best_ms)) {
+        best = c;
+        best_ms = ms;
+      }
+    }
+    if (ms_out) ms_out[c] = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_config[reps - 1][precision].store(out == QSVM_OK ? best : prev);
+  if (out != QSVM_OK) return out;
+  *best_out = best;
   return QSVM_OK;
 }
 

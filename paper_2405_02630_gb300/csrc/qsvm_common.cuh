@@ -52,6 +52,37 @@ struct TileArgs {
   int64_t ldl;
 };
 
+// Runtime pipeline configuration of the pair kernels (the autotuner's knobs):
+// sites per chunk and number of shared-memory stages in flight.
+struct PipeCfg {
+  int S;            // sites per chunk
+  int stages;       // 2..4
+  int slot_bytes;   // S * record bytes + 16 (per point per stage)
+  int stage_bytes;  // 32 points * slot_bytes
+};
+
+// One Gram job of a batch, as the persistent kernel reads it (64 bytes).
+struct DevJob {
+  const uint8_t* mps;
+  int64_t n_points;
+  int64_t tiles;    // tiles per side
+  double* K;
+  int64_t ldk;
+  double* logK;
+  int64_t ldl;
+  int32_t n_qubits;
+  int32_t pad;
+};
+static_assert(sizeof(DevJob) == 64, "DevJob layout");
+
+struct BatchArgs {
+  const DevJob* jobs;
+  const int64_t* prefix;            // n_jobs + 1 tile offsets
+  unsigned long long* counter;      // work-queue head, zeroed before each launch
+  int n_jobs;
+  int64_t total_tiles;
+};
+
 // ---------------------------------------------------------------- PTX ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

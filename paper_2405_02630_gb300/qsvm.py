@@ -39,6 +39,15 @@ _lock = threading.Lock()
 _lib = None
 
 _i32, _i64, _sz, _vp, _dp = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p
+
+
+class QsvmJob(ctypes.Structure):
+    """Mirror of struct qsvm_job (include/qsvm.h)."""
+    _fields_ = [("mps", ctypes.c_void_p), ("n_points", ctypes.c_int64), ("n_qubits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("K", ctypes.c_void_p), ("ldk", ctypes.c_int64),
+                ("logK", ctypes.c_void_p), ("ldl", ctypes.c_int64)]
+
+
 _SIGS = {
     "qsvm_mps_record_bytes": (_sz, [_i32, _i32]),
     "qsvm_mps_bytes": (_sz, [_i32, _i32, _i64, _i32]),
@@ -49,6 +58,18 @@ _SIGS = {
     "qsvm_gram_num_tiles": (_i64, [_i64, _i32, _i32]),
     "qsvm_gram_partition": (_i32, [_i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "qsvm_kernel_gram_tiles": (_i32, [_vp, _i64, _i32, _i32, _i32, _i64, _i64, _dp, _i64, _dp, _i64, _vp]),
+    "qsvm_batch_workspace_bytes": (_sz, [_i32]),
+    "qsvm_kernel_batch": (_i32, [ctypes.POINTER(QsvmJob), _i32, _i32, _i32, _vp, _sz, _vp]),
+    "qsvm_batch_plan_create": (_i32, [ctypes.POINTER(QsvmJob), _i32, _i32, _i32, _vp, _sz,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "qsvm_batch_plan_launch": (_i32, [_vp, _vp]),
+    "qsvm_batch_plan_destroy": (_i32, [_vp]),
+    "qsvm_num_configs": (_i32, []),
+    "qsvm_config_info": (_i32, [_i32, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "qsvm_set_config": (_i32, [_i32, _i32, _i32]),
+    "qsvm_get_config": (_i32, [_i32, _i32]),
+    "qsvm_autotune": (_i32, [_vp, _i64, _i32, _i32, _i32, _dp, _i64, _vp, ctypes.POINTER(_i32),
+                             ctypes.POINTER(ctypes.c_float)]),
     "qsvm_device_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
     "qsvm_last_error": (ctypes.c_char_p, []),
     "qsvm_version": (ctypes.c_char_p, []),
@@ -172,6 +193,86 @@ def qsvm_kernel_cross(mps_a, n_a: int, mps_b, n_b: int, n_qubits: int, reps: int
     _check(lib().qsvm_kernel_cross(_ptr(mps_a), n_a, _ptr(mps_b), n_b, n_qubits, reps, _prec(precision), _ptr(K),
                                    K.stride(0), _ptr(L), L.stride(0) if L is not None else 0, _stream(stream)))
     return K, L
+
+
+# ------------------------------------------------------------------ batch ---
+def _jobs_array(jobs):
+    """jobs: list of dicts with mps (uint8 tensor), n_points, n_qubits, K (tensor), logK (tensor or None)."""
+    arr = (QsvmJob * len(jobs))()
+    for k, j in enumerate(jobs):
+        K, L = j["K"], j.get("logK")
+        arr[k] = QsvmJob(j["mps"].data_ptr(), j["n_points"], j["n_qubits"], 0, K.data_ptr(), K.stride(0),
+                         L.data_ptr() if L is not None else None, L.stride(0) if L is not None else 0)
+    return arr
+
+
+def qsvm_batch_workspace_bytes(n_jobs: int) -> int:
+    return int(lib().qsvm_batch_workspace_bytes(n_jobs))
+
+
+def qsvm_kernel_batch(jobs, reps: int, precision, ws, stream=None):
+    arr = _jobs_array(jobs)
+    _check(lib().qsvm_kernel_batch(arr, len(jobs), reps, _prec(precision), _ptr(ws), ws.numel() * ws.element_size(),
+                                   _stream(stream)))
+
+
+class BatchPlan:
+    """A CUDA-graph replay of one persistent multi-job launch (qsvm_batch_plan_*)."""
+
+    def __init__(self, jobs, reps: int, precision, ws):
+        self._keep = (jobs, ws)  # the plan uses these buffers until destroyed
+        arr = _jobs_array(jobs)
+        h = ctypes.c_void_p()
+        _check(lib().qsvm_batch_plan_create(arr, len(jobs), reps, _prec(precision), _ptr(ws),
+                                            ws.numel() * ws.element_size(), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().qsvm_batch_plan_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            lib().qsvm_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qsvm_batch_plan_create(jobs, reps: int, precision, ws) -> BatchPlan:
+    return BatchPlan(jobs, reps, precision, ws)
+
+
+# ---------------------------------------------------------------- configs ---
+def qsvm_num_configs() -> int:
+    return int(lib().qsvm_num_configs())
+
+
+def qsvm_config_info(index: int, reps: int, precision):
+    s, st = _i32(0), _i32(0)
+    _check(lib().qsvm_config_info(index, reps, _prec(precision), ctypes.byref(s), ctypes.byref(st)))
+    return int(s.value), int(st.value)
+
+
+def qsvm_set_config(reps: int, precision, index: int):
+    _check(lib().qsvm_set_config(reps, _prec(precision), index))
+
+
+def qsvm_get_config(reps: int, precision) -> int:
+    return int(lib().qsvm_get_config(reps, _prec(precision)))
+
+
+def qsvm_autotune(mps, n_points: int, n_qubits: int, reps: int, precision, K, stream=None):
+    """Times every configuration on this Gram, selects the fastest; returns (best, ms list)."""
+    nc = qsvm_num_configs()
+    ms = (ctypes.c_float * nc)()
+    best = _i32(-1)
+    _check(lib().qsvm_autotune(_ptr(mps), n_points, n_qubits, reps, _prec(precision), _ptr(K), K.stride(0),
+                               _stream(stream), ctypes.byref(best), ms))
+    return int(best.value), [float(v) for v in ms]
 
 
 def qsvm_device_status(clear: bool = True, stream=None) -> int:

@@ -89,3 +89,46 @@ def test_partition_errors():
         qsvm.qsvm_gram_partition(100, 2, 0, 2, 2)
     with pytest.raises(qsvm.QsvmError):
         qsvm.qsvm_gram_partition(0, 2, 0, 1, 0)
+
+
+def test_batch_workspace_and_argument_errors():
+    assert qsvm.qsvm_batch_workspace_bytes(0) == 0
+    w1, w32 = qsvm.qsvm_batch_workspace_bytes(1), qsvm.qsvm_batch_workspace_bytes(32)
+    assert w1 % 256 == 0 and w32 % 256 == 0 and w32 >= 256 + 64 * 32 + 8 * 33
+    L = qsvm.lib()
+    job = qsvm.QsvmJob(256, 10, 8, 0, 512, 10, None, 0)
+    arr = (qsvm.QsvmJob * 1)(job)
+    v = ctypes.c_void_p
+    assert L.qsvm_kernel_batch(None, 1, 2, 2, v(4096), 1 << 20, None) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_kernel_batch(arr, 1, 2, 2, v(4096), 16, None) == qsvm.QSVM_ERR_WORKSPACE
+    assert L.qsvm_kernel_batch(arr, 1, 2, 2, v(4100), 1 << 20, None) == qsvm.QSVM_ERR_ARG  # misaligned ws
+    assert L.qsvm_kernel_batch(arr, 1, 4, 2, v(4096), 1 << 20, None) == qsvm.QSVM_ERR_CHI
+    bad = (qsvm.QsvmJob * 1)(qsvm.QsvmJob(256, 10, 8, 0, 512, 9, None, 0))  # ldk < n_points
+    assert L.qsvm_kernel_batch(bad, 1, 2, 2, v(4096), 1 << 20, None) == qsvm.QSVM_ERR_ARG
+    h = ctypes.c_void_p()
+    assert L.qsvm_batch_plan_create(bad, 1, 2, 2, v(4096), 1 << 20, ctypes.byref(h)) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_batch_plan_launch(None, None) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_batch_plan_destroy(None) == qsvm.QSVM_OK
+
+
+def test_configs():
+    n = qsvm.qsvm_num_configs()
+    assert n >= 4
+    for reps in (1, 2, 3):
+        for prec in ("fp64", "fp32", "fp32_split"):
+            for c in range(n):
+                S, st = qsvm.qsvm_config_info(c, reps, prec)
+                assert S >= 1 and 2 <= st <= 4
+    S2, _ = qsvm.qsvm_config_info(1, 2, "fp32_split")
+    assert S2 == 4  # 1 KB of 256-byte records per point and chunk
+    assert qsvm.qsvm_get_config(2, "fp64") == -1
+    qsvm.qsvm_set_config(2, "fp64", 0)
+    assert qsvm.qsvm_get_config(2, "fp64") == 0
+    qsvm.qsvm_set_config(2, "fp64", -1)
+    with pytest.raises(qsvm.QsvmError):
+        qsvm.qsvm_set_config(2, "fp64", n)
+
+
+def test_autotune_buckets():
+    from paper_2405_02630_gb300 import autotune
+    assert [autotune.n_bucket(n) for n in (2, 16, 17, 784)] == [2, 16, 32, 1024]
