@@ -68,21 +68,26 @@ enum qsvm_precision {
 };
 
 /* ---- MPS storage ---------------------------------------------------------
- * An MPS buffer holds n_points * n_qubits site records, point-major:
- * record (i, k) starts at byte (i * n_qubits + k) * qsvm_mps_record_bytes().
  * The feature map ends with a diagonal layer, so the physical index of site k
  * equals the last-repetition spin carried on its right bond: with the right
  * bond index u = 2p + s and left bond index t = 2q + c, the tensor
- * A_k[sigma][t][u] is nonzero only when sigma == s, and the record stores the
+ * A_k[sigma][t][u] is nonzero only when sigma == s.  A site record stores the
  * four chi/2 x chi/2 blocks a_cs[q][p] = A_k[s][2q+c][2p+s], block index
- * b = 2c + s, each row-major over (q, p):
- *   QSVM_FP64        complex128 (re, im) per entry;
- *   QSVM_FP32        complex64 per entry;
- *   QSVM_FP32_SPLIT  per block: chi^2/4 complex64 "hi" entries (re and im on
- *                    the 2^-11 grid), then chi^2/4 complex64 "lo" entries.
- * Site 0 has a left bond of dimension 1 (only t = 0 is nonzero); the last site
- * has a right bond of dimension 2 holding the physical index (u = sigma, p = 0).
- * The layout is private to this library: produce it with qsvm_build_mps. */
+ * b = 2c + s, each row-major over (q, p), 16 bytes per entry:
+ *   QSVM_FP64        (re, im) as two doubles;
+ *   QSVM_FP32        one "form" entry of four floats (below);
+ *   QSVM_FP32_SPLIT  per block: the chi^2/4 "hi" form entries (re and im on the
+ *                    2^-11 grid), then the chi^2/4 "lo" form entries.
+ * qsvm_mps_record_bytes() is the size of one record.  FP64 buffers hold one
+ * record per (point, site), point-major: record (i, k) at byte
+ * (i * n_qubits + k) * record_bytes.  The FP32 formats hold two forms of every
+ * record in two consecutive arrays of that layout: first the row-side a-form,
+ * entry (re, im, -im, re) = (A, iA); then the column-side b-form, entry
+ * (re, -im, im, re) = (conj A, i conj A).  With them a complex multiply-add is
+ * two packed FP32x2 FMAs.  Site 0 has a left bond of dimension 1 (only t = 0 is
+ * nonzero); the last site has a right bond of dimension 2 holding the physical
+ * index (u = sigma, p = 0).  The layout is private to this library: produce it
+ * with qsvm_build_mps and size it with qsvm_mps_bytes. */
 size_t qsvm_mps_record_bytes(int32_t reps, int32_t precision);
 size_t qsvm_mps_bytes(int32_t n_qubits, int32_t reps, int64_t n_points, int32_t precision);
 

@@ -28,25 +28,31 @@ struct cd {
 };
 __device__ __forceinline__ cd cmul(cd a, cd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 
-// Store one complex entry (q, p) of block b in the record, in the requested format.
+// Store one complex entry (q, p) of block b, in the requested format: FP64 once
+// as (re, im); FP32 formats in both forms (recA: a-form (A, iA); recB: b-form
+// (conj A, i conj A)), the split format as hi then lo parts of each block.
+__device__ __forceinline__ void store_forms(uint8_t* pa, uint8_t* pb, float re, float im) {
+  reinterpret_cast<float4*>(pa)[0] = make_float4(re, im, -im, re);
+  reinterpret_cast<float4*>(pb)[0] = make_float4(re, -im, im, re);
+}
+
 template <int CHI, int PREC>
-__device__ __forceinline__ void store_entry(uint8_t* rec, int b, int q, int p, cd v) {
+__device__ __forceinline__ void store_entry(uint8_t* recA, uint8_t* recB, int b, int q, int p, cd v) {
   using Rec = Record<CHI, PREC>;
   constexpr int H = CHI / 2;
-  uint8_t* blk = rec + b * Rec::kBlockBytes;
-  const int e = q * H + p;
+  const int off = b * Rec::kBlockBytes + (q * H + p) * Rec::kEntryBytes;
   if constexpr (PREC == QSVM_FP64) {
-    reinterpret_cast<double2*>(blk)[e] = make_double2(v.re, v.im);
+    reinterpret_cast<double2*>(recA + off)[0] = make_double2(v.re, v.im);
   } else if constexpr (PREC == QSVM_FP32) {
-    reinterpret_cast<float2*>(blk)[e] = make_float2(__double2float_rn(v.re), __double2float_rn(v.im));
+    store_forms(recA + off, recB + off, __double2float_rn(v.re), __double2float_rn(v.im));
   } else {
     // hi: nearest multiple of 2^-kGridT (exact in double and in float since
     // |v| <= 1); lo: the remainder rounded to float.
     constexpr double s = (double)(1 << kGridT);
     const double hr = rint(v.re * s) / s, hi = rint(v.im * s) / s;
-    reinterpret_cast<float2*>(blk)[e] = make_float2((float)hr, (float)hi);
-    reinterpret_cast<float2*>(blk)[H * H + e] =
-        make_float2(__double2float_rn(v.re - hr), __double2float_rn(v.im - hi));
+    store_forms(recA + off, recB + off, (float)hr, (float)hi);
+    store_forms(recA + off + Rec::kPartBytes, recB + off + Rec::kPartBytes, __double2float_rn(v.re - hr),
+                __double2float_rn(v.im - hi));
   }
 }
 
@@ -123,7 +129,8 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
     zzp = cd{ct, -st};  // a = 0: z(a) = +1 -> exp(-i theta) for sigma = 0
     zzm = cd{ct, st};   // a = 1: z(a) = -1 -> exp(+i theta) for sigma = 0
   }
-  uint8_t* rec = mps + gid * Rec::kBytes;
+  uint8_t* recA = mps + gid * Rec::kBytes;
+  uint8_t* recB = recA + (Rec::kForms == 2 ? n_points * (int64_t)n * Rec::kBytes : 0);
   const bool last = (k == n - 1);
   for (int t = 0; t < CHI; ++t) {
     cd v[2][CHI];
@@ -142,7 +149,7 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
       cd val;
       if (last) val = (u < 2) ? v[u][0] : cd{0.0, 0.0};
       else val = v[s][u];
-      store_entry<CHI, PREC>(rec, 2 * c + s, q, p, val);
+      store_entry<CHI, PREC>(recA, recB, 2 * c + s, q, p, val);
     }
   }
 }

@@ -36,24 +36,6 @@ __device__ __forceinline__ const uint8_t* sptr(uint32_t a) {
 }
 
 template <int H>
-__device__ __forceinline__ void load_block_f(uint32_t a, float2 (&d)[H][H]) {
-  const uint8_t* p = sptr(a);
-  if constexpr ((H * H) % 2 == 0) {
-    const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-    for (int e = 0; e < H * H / 2; ++e) {
-      const float4 v = q[e];
-      d[(2 * e) / H][(2 * e) % H] = make_float2(v.x, v.y);
-      d[(2 * e + 1) / H][(2 * e + 1) % H] = make_float2(v.z, v.w);
-    }
-  } else {
-    const float2* q = reinterpret_cast<const float2*>(p);
-#pragma unroll
-    for (int e = 0; e < H * H; ++e) d[e / H][e % H] = q[e];
-  }
-}
-
-template <int H>
 __device__ __forceinline__ void load_block_d(uint32_t a, double2 (&d)[H][H]) {
   const double2* q = reinterpret_cast<const double2*>(sptr(a));
 #pragma unroll
@@ -170,7 +152,35 @@ struct Engine<CHI, QSVM_FP64> {
   }
 };
 
-// Plain FP32: same algebra in float, renormalised every 4 sites.
+// ------------------------------------------------------ packed FP32 ---------
+// FP32x2 operations (one instruction, two lanes, each lane rounded exactly like
+// the scalar __fmaf_rn / __fadd_rn / __fmul_rn).
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+template <int G>
+__device__ __forceinline__ float2 grid_round2(float2 v) {
+  constexpr float C = 1.5f * (float)(1 << (23 - G));
+  return add2(add2(v, make_float2(C, C)), make_float2(-C, -C));
+}
+
+// A block of form entries: first pair (A or conj B), second pair (iA or i conj B).
+template <int H>
+__device__ __forceinline__ void load_forms(uint32_t a, float2 (&x)[H][H], float2 (&ix)[H][H]) {
+  const float4* q = reinterpret_cast<const float4*>(sptr(a));
+#pragma unroll
+  for (int e = 0; e < H * H; ++e) {
+    const float4 v = q[e];
+    x[e / H][e % H] = make_float2(v.x, v.y);
+    ix[e / H][e % H] = make_float2(v.z, v.w);
+  }
+}
+
+// Plain FP32: complex values as (re, im) lane pairs; a complex MAC is two
+// packed FMAs, E A = E.re (A) + E.im (iA) and X conj(B) = X.re (conj B) +
+// X.im (i conj B), with the tensor side read ready-made from the two record
+// forms.  Renormalised every 4 sites.
 template <int CHI>
 struct Engine<CHI, QSVM_FP32> {
   static constexpr int H = CHI / 2;
@@ -202,37 +212,31 @@ struct Engine<CHI, QSVM_FP32> {
     for (int s = 0; s < 2; ++s) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        float2 a[H][H], b[H][H];
-        load_block_f<H>(ra + (2 * c + s) * Rec::kBlockBytes, a);
-        load_block_f<H>(rb + (2 * c + s) * Rec::kBlockBytes, b);
+        float2 A[H][H], iA[H][H], cB[H][H], icB[H][H];
+        load_forms<H>(ra + (2 * c + s) * Rec::kBlockBytes, A, iA);
+        load_forms<H>(rb + (2 * c + s) * Rec::kBlockBytes, cB, icB);
 #pragma unroll
         for (int p = 0; p < H; ++p) {
           float2 X[H];
 #pragma unroll
-          for (int r = 0; r < H; ++r) {
-            float xr = 0.f, xi = 0.f;
+          for (int r = 0; r < H; ++r) {  // X[r] = sum_q a[q][p] E_c[q][r]
+            float2 x = make_float2(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < H; ++q) {
-              const float2 A = a[q][p], e = E[c][q][r];
-              xr = fmaf(A.x, e.x, xr);
-              xr = fmaf(-A.y, e.y, xr);
-              xi = fmaf(A.x, e.y, xi);
-              xi = fmaf(A.y, e.x, xi);
+              x = fma2(bc(E[c][q][r].x), A[q][p], x);
+              x = fma2(bc(E[c][q][r].y), iA[q][p], x);
             }
-            X[r] = make_float2(xr, xi);
+            X[r] = x;
           }
 #pragma unroll
-          for (int pp = 0; pp < H; ++pp) {
-            float nr = N[s][p][pp].x, ni = N[s][p][pp].y;
+          for (int pp = 0; pp < H; ++pp) {  // N_s[p][pp] += sum_r X[r] conj(b[r][pp])
+            float2 acc = N[s][p][pp];
 #pragma unroll
             for (int r = 0; r < H; ++r) {
-              const float2 B = b[r][pp];
-              nr = fmaf(X[r].x, B.x, nr);
-              nr = fmaf(X[r].y, B.y, nr);
-              ni = fmaf(X[r].y, B.x, ni);
-              ni = fmaf(-X[r].x, B.y, ni);
+              acc = fma2(bc(X[r].x), cB[r][pp], acc);
+              acc = fma2(bc(X[r].y), icB[r][pp], acc);
             }
-            N[s][p][pp] = make_float2(nr, ni);
+            N[s][p][pp] = acc;
           }
         }
       }
@@ -256,30 +260,23 @@ struct Engine<CHI, QSVM_FP32> {
     if (!(m > 0.f) || !isfinite(m)) return;
     int e;
     frexpf(m, &e);
-    float sc;
     if (e < -120) {  // subnormal territory: scale in two exact steps
 #pragma unroll
       for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int p = 0; p < H; ++p)
 #pragma unroll
-          for (int r = 0; r < H; ++r) {
-            E[s][p][r].x *= pow2f(100);
-            E[s][p][r].y *= pow2f(100);
-          }
+          for (int r = 0; r < H; ++r) E[s][p][r] = mul2(E[s][p][r], bc(pow2f(100)));
       L -= 100;
       e += 100;
     }
-    sc = pow2f(-e);
+    const float2 sc = bc(pow2f(-e));
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
       for (int p = 0; p < H; ++p)
 #pragma unroll
-        for (int r = 0; r < H; ++r) {
-          E[s][p][r].x *= sc;
-          E[s][p][r].y *= sc;
-        }
+        for (int r = 0; r < H; ++r) E[s][p][r] = mul2(E[s][p][r], sc);
     L += e;
   }
 
@@ -304,7 +301,7 @@ struct Engine<CHI, QSVM_FP32> {
 // where full() is the rounded FP32 sum hi + lo.  Each correction is about 2^-11
 // of the result, so its FP32 rounding costs ~2^-35 relative per site; nothing
 // else is rounded.  This is the split hi+lo compensated product carried out on
-// the FP32 pipe: 12 FMAs per complex MAC.
+// the FP32 pipe: 6 packed FMAs (12 FMAs) per complex MAC.
 template <int CHI>
 struct Engine<CHI, QSVM_FP32_SPLIT> {
   static constexpr int H = CHI / 2;
@@ -326,6 +323,7 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
   }
 
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
+    const float2 m1 = make_float2(-1.f, -1.f);
     float2 Nh[2][H][H], Nl[2][H][H];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -339,40 +337,34 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
       for (int c = 0; c < 2; ++c) {
         const uint32_t pa = ra + (2 * c + s) * Rec::kBlockBytes;
         const uint32_t pb = rb + (2 * c + s) * Rec::kBlockBytes;
-        float2 ah[H][H], al[H][H], bh[H][H], bl[H][H];
-        load_block_f<H>(pa, ah);
-        load_block_f<H>(pa + H * H * 8, al);
-        load_block_f<H>(pb, bh);
-        load_block_f<H>(pb + H * H * 8, bl);
+        float2 Ah[H][H], iAh[H][H], Al[H][H], iAl[H][H];
+        float2 Bh[H][H], iBh[H][H], Bl[H][H], iBl[H][H];  // conj(b) and i conj(b), hi and lo
+        load_forms<H>(pa, Ah, iAh);
+        load_forms<H>(pa + Rec::kPartBytes, Al, iAl);
+        load_forms<H>(pb, Bh, iBh);
+        load_forms<H>(pb + Rec::kPartBytes, Bl, iBl);
         // step 1: X[p][r] = sum_q a[q][p] E_c[q][r]
         float2 Xh[H][H], Xl[H][H], Xf[H][H];
 #pragma unroll
         for (int p = 0; p < H; ++p) {
 #pragma unroll
           for (int r = 0; r < H; ++r) {
-            float hr = 0.f, hi = 0.f, lr = 0.f, li = 0.f;
+            float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < H; ++q) {
-              const float2 A = ah[q][p], Al = al[q][p];
               const float2 e = Eh[c][q][r], el = El[c][q][r], ef = Ef[c][q][r];
-              hr = __fmaf_rn(A.x, e.x, hr);
-              hr = __fmaf_rn(-A.y, e.y, hr);
-              hi = __fmaf_rn(A.x, e.y, hi);
-              hi = __fmaf_rn(A.y, e.x, hi);
-              lr = __fmaf_rn(A.x, el.x, lr);
-              lr = __fmaf_rn(-A.y, el.y, lr);
-              lr = __fmaf_rn(Al.x, ef.x, lr);
-              lr = __fmaf_rn(-Al.y, ef.y, lr);
-              li = __fmaf_rn(A.x, el.y, li);
-              li = __fmaf_rn(A.y, el.x, li);
-              li = __fmaf_rn(Al.x, ef.y, li);
-              li = __fmaf_rn(Al.y, ef.x, li);
+              h = fma2(bc(e.x), Ah[q][p], h);
+              h = fma2(bc(e.y), iAh[q][p], h);
+              l = fma2(bc(el.x), Ah[q][p], l);
+              l = fma2(bc(el.y), iAh[q][p], l);
+              l = fma2(bc(ef.x), Al[q][p], l);
+              l = fma2(bc(ef.y), iAl[q][p], l);
             }
-            const float vr = __fadd_rn(hr, lr), vi = __fadd_rn(hi, li);
-            const float xr = grid_round<GX>(vr), xi = grid_round<GX>(vi);
-            Xh[p][r] = make_float2(xr, xi);
-            Xl[p][r] = make_float2(__fadd_rn(__fsub_rn(hr, xr), lr), __fadd_rn(__fsub_rn(hi, xi), li));
-            Xf[p][r] = make_float2(vr, vi);
+            const float2 v = add2(h, l);
+            const float2 xh = grid_round2<GX>(v);
+            Xh[p][r] = xh;
+            Xl[p][r] = add2(fma2(xh, m1, h), l);  // (h - xh) is exact
+            Xf[p][r] = v;
           }
         }
         // step 2: N_s[p][pp] += sum_r X[p][r] conj(b[r][pp])
@@ -380,25 +372,19 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
         for (int p = 0; p < H; ++p) {
 #pragma unroll
           for (int pp = 0; pp < H; ++pp) {
-            float hr = Nh[s][p][pp].x, hi = Nh[s][p][pp].y, lr = Nl[s][p][pp].x, li = Nl[s][p][pp].y;
+            float2 hh = Nh[s][p][pp], ll = Nl[s][p][pp];
 #pragma unroll
             for (int r = 0; r < H; ++r) {
-              const float2 X = Xh[p][r], Xo = Xl[p][r], Xa = Xf[p][r], B = bh[r][pp], Bl = bl[r][pp];
-              hr = __fmaf_rn(X.x, B.x, hr);
-              hr = __fmaf_rn(X.y, B.y, hr);
-              hi = __fmaf_rn(X.y, B.x, hi);
-              hi = __fmaf_rn(-X.x, B.y, hi);
-              lr = __fmaf_rn(Xa.x, Bl.x, lr);
-              lr = __fmaf_rn(Xa.y, Bl.y, lr);
-              lr = __fmaf_rn(Xo.x, B.x, lr);
-              lr = __fmaf_rn(Xo.y, B.y, lr);
-              li = __fmaf_rn(Xa.y, Bl.x, li);
-              li = __fmaf_rn(-Xa.x, Bl.y, li);
-              li = __fmaf_rn(Xo.y, B.x, li);
-              li = __fmaf_rn(-Xo.x, B.y, li);
+              const float2 xh = Xh[p][r], xl = Xl[p][r], xf = Xf[p][r];
+              hh = fma2(bc(xh.x), Bh[r][pp], hh);
+              hh = fma2(bc(xh.y), iBh[r][pp], hh);
+              ll = fma2(bc(xf.x), Bl[r][pp], ll);
+              ll = fma2(bc(xf.y), iBl[r][pp], ll);
+              ll = fma2(bc(xl.x), Bh[r][pp], ll);
+              ll = fma2(bc(xl.y), iBh[r][pp], ll);
             }
-            Nh[s][p][pp] = make_float2(hr, hi);
-            Nl[s][p][pp] = make_float2(lr, li);
+            Nh[s][p][pp] = hh;
+            Nl[s][p][pp] = ll;
           }
         }
       }
@@ -412,31 +398,29 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
       for (int p = 0; p < H; ++p)
 #pragma unroll
         for (int r = 0; r < H; ++r) {
-          V[s][p][r] = make_float2(__fadd_rn(Nh[s][p][r].x, Nl[s][p][r].x), __fadd_rn(Nh[s][p][r].y, Nl[s][p][r].y));
+          V[s][p][r] = add2(Nh[s][p][r], Nl[s][p][r]);
           m = fmaxf(m, fmaxf(fabsf(V[s][p][r].x), fabsf(V[s][p][r].y)));
         }
     int e = 0;
     if (m > 0.f && isfinite(m)) {
       frexpf(m, &e);
       if (e < -120) {  // collapse to near zero: scale up in two exact steps
+        const float2 up = bc(pow2f(100));
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
           for (int p = 0; p < H; ++p)
 #pragma unroll
             for (int r = 0; r < H; ++r) {
-              Nh[s][p][r].x *= pow2f(100);
-              Nh[s][p][r].y *= pow2f(100);
-              Nl[s][p][r].x *= pow2f(100);
-              Nl[s][p][r].y *= pow2f(100);
-              V[s][p][r].x *= pow2f(100);
-              V[s][p][r].y *= pow2f(100);
+              Nh[s][p][r] = mul2(Nh[s][p][r], up);
+              Nl[s][p][r] = mul2(Nl[s][p][r], up);
+              V[s][p][r] = mul2(V[s][p][r], up);
             }
         L -= 100;
         e += 100;
       }
     }
-    const float sc = pow2f(-e);
+    const float2 sc = bc(pow2f(-e));
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -445,12 +429,11 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
         for (int r = 0; r < H; ++r) {
           // full = (Nh + Nl) 2^-e; hi = grid(full); lo = (Nh 2^-e - hi) + Nl 2^-e, where
           // Nh 2^-e - hi is exact (both on grids whose difference fits in 24 bits)
-          const float fx = __fmul_rn(V[s][p][r].x, sc), fy = __fmul_rn(V[s][p][r].y, sc);
-          const float hx = grid_round<kGridE>(fx), hy = grid_round<kGridE>(fy);
-          Eh[s][p][r] = make_float2(hx, hy);
-          El[s][p][r] = make_float2(__fmaf_rn(Nl[s][p][r].x, sc, __fmaf_rn(Nh[s][p][r].x, sc, -hx)),
-                                    __fmaf_rn(Nl[s][p][r].y, sc, __fmaf_rn(Nh[s][p][r].y, sc, -hy)));
-          Ef[s][p][r] = make_float2(fx, fy);
+          const float2 f = mul2(V[s][p][r], sc);
+          const float2 h = grid_round2<kGridE>(f);
+          Eh[s][p][r] = h;
+          El[s][p][r] = fma2(Nl[s][p][r], sc, fma2(h, m1, mul2(Nh[s][p][r], sc)));
+          Ef[s][p][r] = f;
         }
     L += e;
   }
@@ -731,7 +714,8 @@ __global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>())
     const DevJob& J = args.jobs[lo];
     TileWork w;
     tri_decode(t - args.prefix[lo], J.tiles, w.ti, w.tj);
-    w.mpsA = w.mpsB = J.mps;
+    w.mpsA = J.mps;
+    w.mpsB = J.mps + (Record<CHI, PREC>::kForms == 2 ? J.n_points * (int64_t)J.n_qubits * Record<CHI, PREC>::kBytes : 0);
     w.nA = w.nB = J.n_points;
     w.n = J.n_qubits;
     w.symmetric = 1;

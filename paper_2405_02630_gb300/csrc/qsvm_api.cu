@@ -55,6 +55,11 @@ int32_t check_common(int32_t n_qubits, int32_t reps, int32_t precision) {
 
 int64_t tiles_per_side(int64_t n_points, int tdim) { return (n_points + tdim - 1) / tdim; }
 
+// byte offset of the column-side (b-form) records inside an MPS buffer
+size_t form_b_offset(int64_t n_points, int n_qubits, int reps, int prec) {
+  return record_forms(prec) == 2 ? record_bytes(1 << reps, prec) * (size_t)n_points * (size_t)n_qubits : 0;
+}
+
 // selected pipeline configuration per (reps - 1, precision); -1 = default
 std::atomic<int> g_config[3][3] = {{{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}};
 
@@ -89,7 +94,8 @@ int32_t gram_launch(const void* mps, int64_t n_points, int32_t n_qubits, int32_t
                 (long long)tile_end, (long long)total);
   if (tile_begin == tile_end) return QSVM_OK;
   TileArgs a{};
-  a.mpsA = a.mpsB = static_cast<const uint8_t*>(mps);
+  a.mpsA = static_cast<const uint8_t*>(mps);
+  a.mpsB = a.mpsA + form_b_offset(n_points, n_qubits, reps, precision);
   a.nA = a.nB = n_points;
   a.n = n_qubits;
   a.symmetric = 1;
@@ -189,7 +195,8 @@ size_t qsvm_mps_record_bytes(int32_t reps, int32_t precision) {
 
 size_t qsvm_mps_bytes(int32_t n_qubits, int32_t reps, int64_t n_points, int32_t precision) {
   if (n_qubits < 1 || n_points < 0) return 0;
-  return qsvm_mps_record_bytes(reps, precision) * (size_t)n_qubits * (size_t)n_points;
+  return qsvm_mps_record_bytes(reps, precision) * (size_t)record_forms(precision) * (size_t)n_qubits *
+         (size_t)n_points;
 }
 
 int32_t qsvm_build_mps(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
@@ -278,7 +285,7 @@ int32_t qsvm_kernel_cross(const void* mps_a, int64_t n_a, const void* mps_b, int
   const int64_t Ta = tiles_per_side(n_a, tdim), Tb = tiles_per_side(n_b, tdim);
   TileArgs a{};
   a.mpsA = static_cast<const uint8_t*>(mps_a);
-  a.mpsB = static_cast<const uint8_t*>(mps_b);
+  a.mpsB = static_cast<const uint8_t*>(mps_b) + form_b_offset(n_b, n_qubits, reps, precision);
   a.nA = n_a;
   a.nB = n_b;
   a.n = n_qubits;

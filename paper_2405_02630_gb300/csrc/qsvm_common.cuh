@@ -22,28 +22,38 @@ constexpr int kGridT = 11;
 constexpr int kGridE = 10;
 __host__ __device__ constexpr int grid_x(int chi) { return chi >= 8 ? 8 : 9; }
 
+// Site-record geometry.  FP64 records hold each entry once as (re, im).  The
+// FP32 formats hold two forms of every record, in two arrays (all row-side
+// "a-form" records of the buffer first, then all column-side "b-form" records):
+//   a-form entry (A, iA)              = (re, im, -im, re)
+//   b-form entry (conj B, i conj B)   = (re, -im, im, re)
+// so that a complex multiply-accumulate is two packed FP32x2 FMAs with one
+// broadcast operand:  E A = E.re * A + E.im * (iA),  X conj(B) = X.re * conj(B) + X.im * (i conj(B)).
+// Split FP32 stores, per block, the hi entries then the lo entries, each in form.
 template <int CHI, int PREC>
 struct Record {
   static constexpr int H = CHI / 2;                    // block side
   static constexpr int kEntries = H * H;               // complex entries per block
-  static constexpr int kEntryBytes = (PREC == QSVM_FP64) ? 16 : 8;
-  static constexpr int kBlockBytes = kEntries * kEntryBytes * (PREC == QSVM_FP32_SPLIT ? 2 : 1);
-  static constexpr int kBytes = 4 * kBlockBytes;
+  static constexpr int kForms = (PREC == QSVM_FP64) ? 1 : 2;
+  static constexpr int kEntryBytes = 16;               // (re, im) double, or one form entry of 4 floats
+  static constexpr int kPartBytes = kEntries * kEntryBytes;
+  static constexpr int kBlockBytes = kPartBytes * (PREC == QSVM_FP32_SPLIT ? 2 : 1);
+  static constexpr int kBytes = 4 * kBlockBytes;       // one form of one site
 };
 
 inline size_t record_bytes(int chi, int prec) {
   const size_t h2 = (size_t)(chi / 2) * (chi / 2);
-  const size_t entry = (prec == QSVM_FP64) ? 16 : 8;
-  return 4 * h2 * entry * (prec == QSVM_FP32_SPLIT ? 2 : 1);
+  return 4 * h2 * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1);
 }
+inline int record_forms(int prec) { return prec == QSVM_FP64 ? 1 : 2; }
 
-// Launch arguments of the pair-tile kernels.
+// Launch arguments of the per-tile pair kernel.
 struct TileArgs {
-  const uint8_t* mpsA;   // MPS of the row points (i)
-  const uint8_t* mpsB;   // MPS of the column points (j)
+  const uint8_t* mpsA;   // row points (i): a-form records
+  const uint8_t* mpsB;   // column points (j): b-form records
   int64_t nA, nB;
   int n;                 // sites (qubits)
-  int symmetric;         // 1: upper-triangle tiles of a Gram (mpsA == mpsB)
+  int symmetric;         // 1: upper-triangle tiles of a Gram (same points on both sides)
   int64_t tile_begin;    // first linear tile index of this launch
   int64_t tiles_j;       // tiles per row (cross) or per side (symmetric)
   double* K;

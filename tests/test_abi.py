@@ -18,12 +18,15 @@ def test_exports_every_declared_symbol():
 
 
 def test_record_and_mps_bytes():
-    # chi^2 complex entries per site (half of the dense 2 chi^2 are structural zeros)
+    # chi^2 complex entries per site (half of the dense 2 chi^2 are structural zeros),
+    # 16 bytes each; split FP32 holds hi and lo; FP32 formats hold two forms
     for reps, chi in ((1, 2), (2, 4), (3, 8)):
         assert qsvm.qsvm_mps_record_bytes(reps, "fp64") == chi * chi * 16
-        assert qsvm.qsvm_mps_record_bytes(reps, "fp32") == chi * chi * 8
-        assert qsvm.qsvm_mps_record_bytes(reps, "fp32_split") == chi * chi * 16
-    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 8192 * 784 * 256
+        assert qsvm.qsvm_mps_record_bytes(reps, "fp32") == chi * chi * 16
+        assert qsvm.qsvm_mps_record_bytes(reps, "fp32_split") == chi * chi * 32
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp64") == 8192 * 784 * 256
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32") == 2 * 8192 * 784 * 256
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 2 * 8192 * 784 * 512
     assert qsvm.qsvm_mps_record_bytes(4, "fp64") == 0
     assert qsvm.qsvm_mps_record_bytes(2, 7) == 0
 
@@ -120,7 +123,7 @@ def test_configs():
                 S, st = qsvm.qsvm_config_info(c, reps, prec)
                 assert S >= 1 and 2 <= st <= 4
     S2, _ = qsvm.qsvm_config_info(1, 2, "fp32_split")
-    assert S2 == 4  # 1 KB of 256-byte records per point and chunk
+    assert S2 == 2  # 1 KB of 512-byte records per point and chunk
     assert qsvm.qsvm_get_config(2, "fp64") == -1
     qsvm.qsvm_set_config(2, "fp64", 0)
     assert qsvm.qsvm_get_config(2, "fp64") == 0

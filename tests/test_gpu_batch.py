@@ -83,10 +83,17 @@ def test_every_config_bit_identical(q, reps):
     mps = q.qsvm_build_mps(X, reps, prec)
     q.qsvm_set_config(reps, prec, -1)
     Kdef, _ = q.qsvm_kernel_gram(mps, N, n, reps, prec)
+    ran = 0
     for c in range(q.qsvm_num_configs()):
-        q.qsvm_set_config(reps, prec, c)
+        try:
+            q.qsvm_set_config(reps, prec, c)
+        except q.QsvmError as e:  # the shape needs more shared memory than a CTA has
+            assert e.code == q.QSVM_ERR_ARG
+            continue
         Kc, _ = q.qsvm_kernel_gram(mps, N, n, reps, prec)
         assert torch.equal(Kc, Kdef), c
+        ran += 1
+    assert ran >= 2
     q.qsvm_set_config(reps, prec, -1)
 
 

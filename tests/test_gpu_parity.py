@@ -88,15 +88,24 @@ def test_build_mps_lowprec_formats(q):
     N, n, reps = 5, 33, 2
     X = inputs.mnist_like_features(N, n, 77)
     d = _dev(X)
-    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128)
-    f32 = q.qsvm_build_mps(d, reps, "fp32").cpu().numpy().view(np.complex64)
-    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.complex64).reshape(N * n, 4, 2, 4)
-    hi, lo = spl[:, :, 0, :].reshape(-1), spl[:, :, 1, :].reshape(-1)
-    assert np.array_equal(f32, f64.astype(np.complex64))
+    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, 4, 4)
+    f32 = q.qsvm_build_mps(d, reps, "fp32").cpu().numpy().view(np.float32).reshape(2, N * n, 4, 4, 4)
+    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(2, N * n, 4, 2, 4, 4)
+
+    def check_forms(a, b):  # a-form (re, im, -im, re); b-form (re, -im, im, re)
+        re, im = a[..., 0], a[..., 1]
+        assert np.array_equal(a[..., 2], -im) and np.array_equal(a[..., 3], re)
+        assert np.array_equal(b[..., 0], re) and np.array_equal(b[..., 1], -im)
+        assert np.array_equal(b[..., 2], im) and np.array_equal(b[..., 3], re)
+        return re.astype(np.float64) + 1j * im.astype(np.float64)
+
+    v32 = check_forms(f32[0], f32[1])
+    assert np.array_equal(v32, f64.astype(np.complex64).astype(np.complex128))
+    hi = check_forms(spl[0, :, :, 0], spl[1, :, :, 0])
+    lo = check_forms(spl[0, :, :, 1], spl[1, :, :, 1])
     for part in (hi.real, hi.imag):
-        assert np.array_equal(np.round(part.astype(np.float64) * 2048) / 2048, part)
-    rec = hi.astype(np.complex128) + lo.astype(np.complex128)
-    assert np.max(np.abs(rec - f64)) <= 2 ** -34
+        assert np.array_equal(np.round(part * 2048) / 2048, part)
+    assert np.max(np.abs(hi + lo - f64)) <= 2 ** -34
 
 
 # ----------------------------------------------------------- small Grams ---
