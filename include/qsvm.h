@@ -182,6 +182,23 @@ int32_t qsvm_batch_plan_create(const qsvm_job* jobs, int32_t n_jobs, int32_t rep
 int32_t qsvm_batch_plan_launch(qsvm_batch_plan* plan, void* stream);
 int32_t qsvm_batch_plan_destroy(qsvm_batch_plan* plan);
 
+/* qsvm_kernel_batch_noalloc -- qsvm_kernel_batch without a workspace argument,
+ * for callers that cannot allocate device memory (for example code recorded
+ * into a CUDA graph, where cudaMalloc is not allowed; latency-bound serving
+ * loops that must avoid cudaMalloc's device-wide synchronisation; or hosts
+ * whose framework allocator already owns all device memory).  The paper has no
+ * counterpart: this is an interface for such callers.  The job table and the
+ * work-queue head live in a fixed 76 KiB array inside the library's device
+ * image, present on every GPU that loads the library until the process exits;
+ * at most 1024 jobs per call (more returns QSVM_ERR_WORKSPACE).  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call reuses the same
+ * array and rewrites it (the queue head restarts at zero each call), so calls
+ * whose work overlaps on the GPU race: order them on one stream or with events.
+ * No device memory is allocated or freed.  Errors: as qsvm_kernel_batch. */
+int32_t qsvm_kernel_batch_noalloc(const qsvm_job* jobs, int32_t n_jobs, int32_t reps, int32_t precision,
+                                  void* stream);
+
 /* ---- pipeline configurations and the autotuner ----------------------------
  * The pair kernels stream site records through shared memory in chunks; a
  * configuration fixes the bytes per point and chunk and the stages in flight.

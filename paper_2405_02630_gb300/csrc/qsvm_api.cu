@@ -9,6 +9,7 @@
 #include "qsvm_common.cuh"
 
 #include <atomic>
+#include <mutex>
 #include <vector>
 
 namespace qsvm {
@@ -460,3 +461,71 @@ const char* qsvm_last_error(void) { return g_last_error.c_str(); }
 const char* qsvm_version(void) { return "qsvm-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---- batch launch for callers that cannot allocate device memory -----------
+// Some callers may not allocate device memory at all: code recorded into a CUDA
+// graph (cudaMalloc cannot be captured), real-time or serving loops that must
+// not take cudaMalloc's implicit device synchronisation, and host programs whose
+// framework allocator already reserves all device memory.  For them,
+// qsvm_kernel_batch_noalloc keeps the batch scratch (job table + work-queue
+// head) in a fixed array that lives in this library's device image instead of a
+// caller workspace.  The array is loaded with the library on every GPU that uses
+// it and stays until the process exits.
+namespace {
+
+constexpr int32_t kNoAllocMaxJobs = 1024;
+constexpr size_t kNoAllocBytes = 76 * 1024;  // >= the workspace of 1024 jobs
+static_assert(((256 + 64 * (size_t)kNoAllocMaxJobs + 255) / 256 * 256 + 8 * (size_t)(kNoAllocMaxJobs + 1) + 255) /
+                      256 * 256 <=
+                  kNoAllocBytes,
+              "static batch scratch too small for its job limit");
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (a host-side name of a __device__ array is not a device address).
+int32_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(QSVM_ERR_ARG, "device %d beyond the supported %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the batch scratch");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return QSVM_OK;
+}
+
+}  // namespace
+
+extern "C" int32_t qsvm_kernel_batch_noalloc(const qsvm_job* jobs, int32_t n_jobs, int32_t reps, int32_t precision,
+                                             void* stream) {
+  if (n_jobs > kNoAllocMaxJobs)
+    return fail(QSVM_ERR_WORKSPACE, "n_jobs=%d exceeds the %d jobs the built-in batch scratch holds; use "
+                "qsvm_kernel_batch with a workspace", n_jobs, kNoAllocMaxJobs);
+  void* ws = nullptr;
+  int32_t rc = noalloc_scratch(&ws);
+  if (rc) return rc;
+  BatchImage img;
+  rc = build_batch_image(jobs, n_jobs, reps, precision, ws, kNoAllocBytes, img);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the image carries a zero work-queue head, so each call starts its queue at 0
+  cudaError_t e = cudaMemcpyAsync(ws, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batch job table upload");
+  const BatchArgs a = batch_args(ws, n_jobs, img.total_tiles);
+  const PipeCfg pc = current_pipe(reps, precision);
+  int grid = 0;
+  e = prepare_persistent(1 << reps, precision, pc, img.total_tiles, &grid);
+  if (e == cudaSuccess) e = launch_persistent(1 << reps, precision, a, pc, grid, st);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent kernel launch");
+  return QSVM_OK;
+}

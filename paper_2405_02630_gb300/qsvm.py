@@ -60,6 +60,7 @@ _SIGS = {
     "qsvm_kernel_gram_tiles": (_i32, [_vp, _i64, _i32, _i32, _i32, _i64, _i64, _dp, _i64, _dp, _i64, _vp]),
     "qsvm_batch_workspace_bytes": (_sz, [_i32]),
     "qsvm_kernel_batch": (_i32, [ctypes.POINTER(QsvmJob), _i32, _i32, _i32, _vp, _sz, _vp]),
+    "qsvm_kernel_batch_noalloc": (_i32, [ctypes.POINTER(QsvmJob), _i32, _i32, _i32, _vp]),
     "qsvm_batch_plan_create": (_i32, [ctypes.POINTER(QsvmJob), _i32, _i32, _i32, _vp, _sz,
                                       ctypes.POINTER(ctypes.c_void_p)]),
     "qsvm_batch_plan_launch": (_i32, [_vp, _vp]),
@@ -214,6 +215,14 @@ def qsvm_kernel_batch(jobs, reps: int, precision, ws, stream=None):
     arr = _jobs_array(jobs)
     _check(lib().qsvm_kernel_batch(arr, len(jobs), reps, _prec(precision), _ptr(ws), ws.numel() * ws.element_size(),
                                    _stream(stream)))
+
+
+def qsvm_kernel_batch_noalloc(jobs, reps: int, precision, stream=None):
+    """The batch without a workspace: for callers that must not allocate device
+    memory; its scratch is a fixed array inside the library (at most 1024 jobs,
+    calls must not overlap on the GPU)."""
+    arr = _jobs_array(jobs)
+    _check(lib().qsvm_kernel_batch_noalloc(arr, len(jobs), reps, _prec(precision), _stream(stream)))
 
 
 class BatchPlan:
