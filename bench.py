@@ -193,19 +193,17 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     td = qsvm.qsvm_gram_tile_dim(reps, P)
-    T = -(-N // td)
-    pairs_rank = 0
-    # pairs in this rank's tile range
-    b = 0
-    for ti in range(T):
-        row = T - ti
-        lo, hi = max(tb, b), min(te, b + row)
-        if lo < hi:
-            ni = min(td, N - ti * td)
-            for tj in range(ti + (lo - b), ti + (hi - b)):
-                nj = min(td, N - tj * td)
-                pairs_rank += ni * (ni + 1) // 2 if tj == ti else ni * nj
-        b += row
+
+    def tiles_pairs(lo, hi):
+        # pairs contracted by tiles [lo, hi) of the Gram's tile order
+        tot = 0
+        for bb in range(lo, hi):
+            ti, tj = qsvm.qsvm_gram_tile_coords(N, reps, P, bb)
+            ni, nj = min(td, N - ti * td), min(td, N - tj * td)
+            tot += ni * (ni + 1) // 2 if ti == tj else ni * nj
+        return tot
+
+    pairs_rank = tiles_pairs(tb, te)
     total_pairs = N * (N + 1) // 2
 
     def step(prec_code=P, tile_range=(tb, te)):
@@ -313,14 +311,7 @@ def run_ours(args):
             qsvm.qsvm_kernel_gram_tiles(mps64, N, n, reps, "fp64", 0, nt, K64)
             e1.record()
             torch.cuda.synchronize()
-            sub_pairs = 0
-            for bb in range(nt):
-                r, rem = 0, bb
-                while rem >= T - r:
-                    rem -= T - r
-                    r += 1
-                ni, nj = min(td, N - r * td), min(td, N - (r + rem) * td)
-                sub_pairs += ni * (ni + 1) // 2 if rem == 0 else ni * nj
+            sub_pairs = tiles_pairs(0, nt)
             fp64_rate = sub_pairs / (e0.elapsed_time(e1) * 1e-3)
             m = ~torch.isnan(K64)
             line["fp64_same_gpu"] = {"entries_per_s": fp64_rate, "tiles_timed": nt,

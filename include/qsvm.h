@@ -130,16 +130,21 @@ int32_t qsvm_kernel_cross(const void* mps_a, int64_t n_a, const void* mps_b, int
 
 /* ---- sharding the symmetric Gram over independent workers ----------------
  * The upper-triangle pair tiles of a Gram are independent (Sec. 5: pairs are
- * distributed evenly over GPUs and the results gathered).  Tiles are numbered
- * row-major over the upper triangle of a T x T tile grid, T = ceil(n_points /
- * qsvm_gram_tile_dim()).  qsvm_gram_partition splits [0, tiles) into `world`
- * contiguous ranges of near-equal pair count; qsvm_kernel_gram_tiles computes
- * one range (writing both K[i][j] and its mirror for every pair in it).  These
- * three are pure host functions except qsvm_kernel_gram_tiles. */
+ * distributed evenly over GPUs and the results gathered).  A tile is a
+ * qsvm_gram_tile_dim() x qsvm_gram_tile_dim() block of pairs; with
+ * T = ceil(n_points / tile_dim), tiles (ti, tj), ti <= tj, are numbered in bands
+ * of 8 tile rows, within a band column by column, within a column row by row
+ * (the order the kernels visit them in; qsvm_gram_tile_coords decodes it).
+ * qsvm_gram_partition splits [0, tiles) into `world` contiguous ranges of
+ * near-equal pair count; qsvm_kernel_gram_tiles computes one range (writing both
+ * K[i][j] and its mirror for every pair in it).  All but qsvm_kernel_gram_tiles
+ * are pure host functions. */
 int32_t qsvm_gram_tile_dim(int32_t reps, int32_t precision);
 int64_t qsvm_gram_num_tiles(int64_t n_points, int32_t reps, int32_t precision);
 int32_t qsvm_gram_partition(int64_t n_points, int32_t reps, int32_t precision, int32_t world, int32_t rank,
                             int64_t* tile_begin, int64_t* tile_end);
+int32_t qsvm_gram_tile_coords(int64_t n_points, int32_t reps, int32_t precision, int64_t tile, int64_t* ti,
+                              int64_t* tj);
 int32_t qsvm_kernel_gram_tiles(const void* mps, int64_t n_points, int32_t n_qubits, int32_t reps,
                                int32_t precision, int64_t tile_begin, int64_t tile_end, double* K, int64_t ldk,
                                double* logK, int64_t ldl, void* stream);

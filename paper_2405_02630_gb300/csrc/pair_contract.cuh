@@ -450,19 +450,6 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
 // Device status word of this translation unit (QSVM_OK or QSVM_ERR_TIMEOUT).
 __device__ int32_t g_pair_status;
 
-// Upper-triangle tile index b (row-major, T tiles per side) -> (ti, tj), ti <= tj.
-__device__ __forceinline__ void tri_decode(int64_t b, int64_t T, int64_t& ti, int64_t& tj) {
-  const double tt = 2.0 * (double)T + 1.0;
-  int64_t r = (int64_t)floor((tt - sqrt(tt * tt - 8.0 * (double)b)) * 0.5);
-  if (r < 0) r = 0;
-  if (r > T - 1) r = T - 1;
-  // start(r) = r*T - r(r-1)/2 ; fix rounding
-  while (r > 0 && r * T - r * (r - 1) / 2 > b) --r;
-  while (r + 1 < T && (r + 1) * T - (r + 1) * r / 2 <= b) ++r;
-  ti = r;
-  tj = r + (b - (r * T - r * (r - 1) / 2));
-}
-
 constexpr int kTI = 16;               // a tile is kTI x kTI pairs, one per thread
 constexpr int kTileThreads = kTI * kTI;
 constexpr int kTileWarps = kTileThreads / 32;
@@ -668,12 +655,8 @@ __global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>())
   tile_ctl_init(ctl, pc);
   const int64_t b = args.tile_begin + blockIdx.x;
   TileWork w;
-  if (args.symmetric) {
-    tri_decode(b, args.tiles_j, w.ti, w.tj);
-  } else {
-    w.ti = b / args.tiles_j;
-    w.tj = b - w.ti * args.tiles_j;
-  }
+  if (args.symmetric) sym_tile_decode(b, args.tiles_j, w.ti, w.tj);
+  else rect_tile_decode(b, args.tiles_i, args.tiles_j, w.ti, w.tj);
   w.mpsA = args.mpsA;
   w.mpsB = args.mpsB;
   w.nA = args.nA;
@@ -713,7 +696,7 @@ __global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>())
     }
     const DevJob& J = args.jobs[lo];
     TileWork w;
-    tri_decode(t - args.prefix[lo], J.tiles, w.ti, w.tj);
+    sym_tile_decode(t - args.prefix[lo], J.tiles, w.ti, w.tj);
     w.mpsA = J.mps;
     w.mpsB = J.mps + (Record<CHI, PREC>::kForms == 2 ? J.n_points * (int64_t)J.n_qubits * Record<CHI, PREC>::kBytes : 0);
     w.nA = w.nB = J.n_points;

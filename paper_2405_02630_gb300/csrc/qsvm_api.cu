@@ -68,7 +68,7 @@ PipeCfg current_pipe(int reps, int prec) { return make_pipe(1 << reps, prec, g_c
 
 constexpr int kMaxSmemPerCta = 227 * 1024;
 
-// pairs contracted by upper-triangle tile b of a T x T grid over n_points
+// pairs contracted by upper-triangle tile (ti, tj) of a T x T grid over n_points
 int64_t tile_pairs(int64_t ti, int64_t tj, int64_t n_points, int tdim) {
   const int64_t ni = std::min<int64_t>(tdim, n_points - ti * tdim);
   const int64_t nj = std::min<int64_t>(tdim, n_points - tj * tdim);
@@ -237,24 +237,34 @@ int32_t qsvm_gram_partition(int64_t n_points, int32_t reps, int32_t precision, i
   const int64_t T = tiles_per_side(n_points, tdim);
   const int64_t total_tiles = T * (T + 1) / 2;
   const int64_t total_pairs = n_points * (n_points + 1) / 2;
-  // boundary r sits at the first tile whose prefix pair count reaches r/world of
-  // the total (tiles are whole, so shares differ by at most one tile)
+  // boundary r sits at the first tile (in tile order) whose prefix pair count
+  // reaches r/world of the total (tiles are whole, so shares differ by at most one tile)
   auto boundary = [&](int64_t r) -> int64_t {
     if (r <= 0) return 0;
     if (r >= world) return total_tiles;
     const double target = (double)total_pairs * (double)r / (double)world;
-    int64_t b = 0;
     double acc = 0;
-    for (int64_t ti = 0; ti < T; ++ti)
-      for (int64_t tj = ti; tj < T; ++tj) {
-        if (acc >= target) return b;
-        acc += (double)tile_pairs(ti, tj, n_points, tdim);
-        ++b;
-      }
+    for (int64_t b = 0; b < total_tiles; ++b) {
+      if (acc >= target) return b;
+      int64_t ti, tj;
+      sym_tile_decode(b, T, ti, tj);
+      acc += (double)tile_pairs(ti, tj, n_points, tdim);
+    }
     return total_tiles;
   };
   *tile_begin = boundary(rank);
   *tile_end = boundary(rank + 1);
+  return QSVM_OK;
+}
+
+int32_t qsvm_gram_tile_coords(int64_t n_points, int32_t reps, int32_t precision, int64_t tile, int64_t* ti,
+                              int64_t* tj) {
+  if (!ti || !tj) return fail(QSVM_ERR_ARG, "null output pointer");
+  const int64_t total = qsvm_gram_num_tiles(n_points, reps, precision);
+  if (total <= 0) return fail(QSVM_ERR_ARG, "no tiles for n_points=%lld reps=%d precision=%d", (long long)n_points,
+                              reps, precision);
+  if (tile < 0 || tile >= total) return fail(QSVM_ERR_ARG, "tile %lld outside [0, %lld)", (long long)tile, (long long)total);
+  sym_tile_decode(tile, tiles_per_side(n_points, qsvm_gram_tile_dim(reps, precision)), *ti, *tj);
   return QSVM_OK;
 }
 
@@ -292,6 +302,7 @@ int32_t qsvm_kernel_cross(const void* mps_a, int64_t n_a, const void* mps_b, int
   a.n = n_qubits;
   a.symmetric = 0;
   a.tile_begin = 0;
+  a.tiles_i = Ta;
   a.tiles_j = Tb;
   a.K = K;
   a.ldk = ldk;

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "../../include/qsvm.h"
@@ -47,6 +48,56 @@ inline size_t record_bytes(int chi, int prec) {
 }
 inline int record_forms(int prec) { return prec == QSVM_FP64 ? 1 : 2; }
 
+// ---- tile order --------------------------------------------------------------
+// Pair tiles are visited in bands of kBandRows tile rows; within a band column by
+// column, within a column row by row.  The CTAs resident at one time then cover a
+// few columns of one band, so each column point's site records are fetched from
+// DRAM about once per band instead of once per tile row.
+constexpr int64_t kBandRows = 8;
+
+// Symmetric Gram (tiles ti <= tj of a T x T grid): tiles before band k (all
+// bands before k are full): band m holds G(G+1)/2 + G(T - mG - G) tiles.
+__host__ __device__ inline int64_t sym_band_start(int64_t k, int64_t T) {
+  const int64_t G = kBandRows;
+  return k * (G * (G + 1) / 2 + G * (T - G)) - G * G * k * (k - 1) / 2;
+}
+
+__host__ __device__ inline void sym_tile_decode(int64_t b, int64_t T, int64_t& ti, int64_t& tj) {
+  const int64_t G = kBandRows;
+  int64_t lo = 0, hi = (T + G - 1) / G - 1;  // last band whose start is <= b
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (sym_band_start(mid, T) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const int64_t r0 = lo * G;
+  const int64_t g = (T - r0) < G ? (T - r0) : G;
+  int64_t o = b - sym_band_start(lo, T);
+  const int64_t tri = g * (g + 1) / 2;
+  if (o < tri) {  // the band's triangle: column c holds rows r0 .. r0 + c
+    int64_t c = (int64_t)((sqrt(8.0 * (double)o + 1.0) - 1.0) * 0.5);
+    while (c > 0 && c * (c + 1) / 2 > o) --c;
+    while ((c + 1) * (c + 2) / 2 <= o) ++c;
+    tj = r0 + c;
+    ti = r0 + (o - c * (c + 1) / 2);
+  } else {        // full columns of g tiles each
+    o -= tri;
+    tj = r0 + g + o / g;
+    ti = r0 + o % g;
+  }
+}
+
+// Cross kernel (Ta x Tb tiles, all of them): bands of G rows, column by column.
+__host__ __device__ inline void rect_tile_decode(int64_t b, int64_t Ta, int64_t Tb, int64_t& ti, int64_t& tj) {
+  const int64_t G = kBandRows;
+  const int64_t k = b / (G * Tb);
+  const int64_t r0 = k * G;
+  const int64_t g = (Ta - r0) < G ? (Ta - r0) : G;
+  const int64_t o = b - k * G * Tb;
+  tj = o / g;
+  ti = r0 + o % g;
+}
+
 // Launch arguments of the per-tile pair kernel.
 struct TileArgs {
   const uint8_t* mpsA;   // row points (i): a-form records
@@ -55,7 +106,8 @@ struct TileArgs {
   int n;                 // sites (qubits)
   int symmetric;         // 1: upper-triangle tiles of a Gram (same points on both sides)
   int64_t tile_begin;    // first linear tile index of this launch
-  int64_t tiles_j;       // tiles per row (cross) or per side (symmetric)
+  int64_t tiles_i;       // tile rows (cross)
+  int64_t tiles_j;       // tile columns (cross) or tiles per side (symmetric)
   double* K;
   int64_t ldk;
   double* logK;          // nullable

@@ -57,6 +57,7 @@ _SIGS = {
     "qsvm_gram_tile_dim": (_i32, [_i32, _i32]),
     "qsvm_gram_num_tiles": (_i64, [_i64, _i32, _i32]),
     "qsvm_gram_partition": (_i32, [_i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "qsvm_gram_tile_coords": (_i32, [_i64, _i32, _i32, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "qsvm_kernel_gram_tiles": (_i32, [_vp, _i64, _i32, _i32, _i32, _i64, _i64, _dp, _i64, _dp, _i64, _vp]),
     "qsvm_batch_workspace_bytes": (_sz, [_i32]),
     "qsvm_kernel_batch": (_i32, [ctypes.POINTER(QsvmJob), _i32, _i32, _i32, _vp, _sz, _vp]),
@@ -144,6 +145,13 @@ def qsvm_gram_partition(n_points: int, reps: int, precision, world: int, rank: i
     _check(lib().qsvm_gram_partition(n_points, reps, _prec(precision), world, rank, ctypes.byref(b),
                                      ctypes.byref(e)))
     return int(b.value), int(e.value)
+
+
+def qsvm_gram_tile_coords(n_points: int, reps: int, precision, tile: int):
+    """(ti, tj) of Gram tile `tile` in the kernels' tile order."""
+    a, b = _i64(0), _i64(0)
+    _check(lib().qsvm_gram_tile_coords(n_points, reps, _prec(precision), tile, ctypes.byref(a), ctypes.byref(b)))
+    return int(a.value), int(b.value)
 
 
 # ---------------------------------------------------------------- compute ---

@@ -62,14 +62,24 @@ def test_build_and_cross_argument_errors():
 
 
 def _tile_pairs(b, N, T, td):
-    # row-major upper triangle of a T x T tile grid
-    r = 0
-    while b >= T - r:
-        b -= T - r
-        r += 1
-    ti, tj = r, r + b
+    ti, tj = qsvm.qsvm_gram_tile_coords(N, 2, "fp32_split", b)
     ni, nj = min(td, N - ti * td), min(td, N - tj * td)
     return ni * (ni + 1) // 2 if ti == tj else ni * nj
+
+
+@pytest.mark.parametrize("N", [1, 16, 17, 100, 129, 1000, 2049])
+def test_tile_order_covers_upper_triangle_once(N):
+    td = qsvm.qsvm_gram_tile_dim(2, "fp32_split")
+    T = -(-N // td)
+    total = qsvm.qsvm_gram_num_tiles(N, 2, "fp32_split")
+    seen = [qsvm.qsvm_gram_tile_coords(N, 2, "fp32_split", b) for b in range(total)]
+    assert len(set(seen)) == total == T * (T + 1) // 2
+    assert all(0 <= ti <= tj < T for ti, tj in seen)
+    # bands of 8 tile rows, visited in order
+    bands = [ti // 8 for ti, _ in seen]
+    assert bands == sorted(bands)
+    with pytest.raises(qsvm.QsvmError):
+        qsvm.qsvm_gram_tile_coords(N, 2, "fp32_split", total)
 
 
 @pytest.mark.parametrize("N,world", [(1, 1), (17, 2), (100, 3), (1000, 8), (8192, 4), (33, 7)])

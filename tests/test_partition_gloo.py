@@ -15,11 +15,8 @@ torch = pytest.importorskip("torch")
 
 
 def _tile_to_pairs(b, N, T, td):
-    r = 0
-    while b >= T - r:
-        b -= T - r
-        r += 1
-    ti, tj = r, r + b
+    from paper_2405_02630_gb300 import qsvm
+    ti, tj = qsvm.qsvm_gram_tile_coords(N, 2, "fp32_split", b)
     pairs = []
     for i in range(ti * td, min(N, (ti + 1) * td)):
         for j in range(tj * td, min(N, (tj + 1) * td)):
