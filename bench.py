@@ -140,6 +140,8 @@ def run_reference(args):
         return 0
     from oracle import oracle
     oracle.build()
+    if args.workload == "batch_cfg3":
+        return run_reference_batch(args)
     X, _, n, reps = inputs.workload(args.workload)
     N = X.shape[0]
     cores = oracle.max_threads()
@@ -166,6 +168,38 @@ def run_reference(args):
     return 0
 
 
+def run_reference_batch(args):
+    """CPU oracle on the 32-job batch: per step, a random sample of each job's pairs
+    in proportion to its share of the batch's pairs."""
+    from oracle import oracle
+    spec = inputs.batch_jobs(seed=3)
+    sizes = [X.shape[0] * (X.shape[0] + 1) // 2 for X, _ in spec]
+    total = sum(sizes)
+    rng = np.random.default_rng(5)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t = 0.0
+        for (X, n), sz in zip(spec, sizes):
+            k = max(1, int(round(args.ref_pairs * sz / total)))
+            a, b = rng.integers(0, X.shape[0], k), rng.integers(0, X.shape[0], k)
+            t0 = time.perf_counter()
+            oracle.mps_pairs(X, X, np.minimum(a, b), np.maximum(a, b), 2)
+            t += time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(t)
+    per_step = sum(times) / len(times)
+    value = args.ref_pairs / per_step
+    print(json.dumps({
+        "impl": "reference", "metric": "gram_entries_per_s", "value": value, "unit": "entries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batch_cfg3", "jobs": len(spec), "reps": 2},
+        "cpu_baseline": {"value": value, "unit": "entries/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"~{args.ref_pairs} pairs per step, drawn from every job by its share"},
+        "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -181,14 +215,21 @@ def run_ours(args):
     qbuild.build()
     qsvm.lib()
 
-    X, _, n, reps = inputs.workload(args.workload)
+    X, Xte, n, reps = inputs.workload(args.workload)
     N = X.shape[0]
+    Nte = 0 if Xte is None else Xte.shape[0]
     prec = args.precision
     P = qsvm.PRECISIONS[prec]
     Xd = torch.from_numpy(X).to(dev)
     mps = torch.empty(qsvm.qsvm_mps_bytes(n, reps, N, P), dtype=torch.uint8, device=dev)
     K = torch.empty((N, N), dtype=torch.float64, device=dev)
     tb, te = qsvm.qsvm_gram_partition(N, reps, P, world, rank)
+    # test x train cross kernel (workloads with a test set): rows split evenly over ranks
+    a0, a1 = (Nte * rank) // world, (Nte * (rank + 1)) // world
+    if Nte:
+        Xted = torch.from_numpy(Xte).to(dev)
+        mps_te = torch.empty(qsvm.qsvm_mps_bytes(n, reps, Nte, P), dtype=torch.uint8, device=dev)
+        Kx = torch.empty((Nte, N), dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -203,14 +244,20 @@ def run_ours(args):
             tot += ni * (ni + 1) // 2 if ti == tj else ni * nj
         return tot
 
-    pairs_rank = tiles_pairs(tb, te)
-    total_pairs = N * (N + 1) // 2
+    pairs_rank = tiles_pairs(tb, te) + (a1 - a0) * N
+    total_pairs = N * (N + 1) // 2 + Nte * N
 
     def step(prec_code=P, tile_range=(tb, te)):
         qsvm.qsvm_build_mps(Xd, reps, prec_code, mps=mps, stream=stream)
+        if Nte:
+            qsvm.qsvm_build_mps(Xted, reps, prec_code, mps=mps_te, stream=stream)
         ev_mid = torch.cuda.Event(enable_timing=True)
         ev_mid.record(stream)
         qsvm.qsvm_kernel_gram_tiles(mps, N, n, reps, prec_code, tile_range[0], tile_range[1], K, stream=stream)
+        if Nte and a1 > a0:
+            rec = qsvm.qsvm_mps_record_bytes(reps, prec_code)
+            qsvm.qsvm_kernel_cross(mps_te[a0 * n * rec:], a1 - a0, mps, N, n, reps, prec_code, K=Kx[a0:a1],
+                                   stream=stream)
         return ev_mid
 
     def barrier():
@@ -277,11 +324,12 @@ def run_ours(args):
         "scaling": "strong", "vs_baseline": None, "dtype": {"fp32_split": "f32x2-split", "fp32": "f32",
                                                             "fp64": "f64"}[prec],
         "data": "synthetic",
-        "config": {"workload": args.workload, "n_qubits": n, "reps": reps, "n_points": N, "precision": prec,
-                   "entries": "unique pairs i<=j incl. diagonal", "l2": "flushed (512 MB write) between timed steps",
-                   "parallelism": f"tiles{world}"},
+        "config": {"workload": args.workload, "n_qubits": n, "reps": reps, "n_points": N, "n_test": Nte,
+                   "precision": prec,
+                   "entries": "unique Gram pairs i<=j incl. diagonal" + (" + test x train" if Nte else ""),
+                   "l2": "flushed (512 MB write) between timed steps", "parallelism": f"tiles{world}"},
         "roofline": roofline,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (4 if Nte else 2) * args.steps,
         "clocks": clocks,
         "pair_kernel_ms": kms,
         "qubit_pair_sites_per_s": value * n,
@@ -291,16 +339,32 @@ def run_ours(args):
         # accuracy of this run against the CPU oracle on sampled pairs
         from oracle import oracle
         rng = np.random.default_rng(7)
-        di = rng.choice(N, 256, replace=False)
-        ia = np.concatenate([di, rng.integers(0, N, 256)])
-        ib = np.concatenate([di, rng.integers(0, N, 256)])
+        ns = min(256, N)
+        di = rng.choice(N, ns, replace=False)
+        ia = np.concatenate([di, rng.integers(0, N, ns)])
+        ib = np.concatenate([di, rng.integers(0, N, ns)])
         Ko, _ = oracle.mps_pairs(X, X, ia, ib, reps)
         Kg = K[torch.from_numpy(ia).to(dev), torch.from_numpy(ib).to(dev)].cpu().numpy()
-        line["accuracy_vs_oracle"] = {"pairs": int(ia.size), "max_abs_dK": float(np.max(np.abs(Kg - Ko))),
-                                      "max_abs_diag_minus_1": float(np.max(np.abs(np.diag(K.cpu().numpy()) - 1)))}
+        acc = {"pairs": int(ia.size), "max_abs_dK": float(np.max(np.abs(Kg - Ko))),
+               "max_abs_diag_minus_1": float(np.max(np.abs(np.diag(K.cpu().numpy()) - 1)))}
+        if Nte:
+            xa, xb = rng.integers(0, Nte, ns), rng.integers(0, N, ns)
+            Kxo, _ = oracle.mps_pairs(Xte, X, xa, xb, reps)
+            Kxg = Kx[torch.from_numpy(xa).to(dev), torch.from_numpy(xb).to(dev)].cpu().numpy()
+            acc["cross_pairs"] = int(ns)
+            acc["cross_max_abs_dK"] = float(np.max(np.abs(Kxg - Kxo)))
+        # near-duplicate pairs, K spread over (0, 1): where |dK| is informative
+        base = inputs.mnist_like_features(24, n, 21) if n >= 64 else inputs.uniform_features(24, n, 21)
+        pert = inputs.near_duplicates(base, 22)
+        Knd_o, _ = oracle.mps_cross(base, pert, reps)
+        Knd, _ = qsvm.cross(torch.from_numpy(base).to(dev), torch.from_numpy(pert).to(dev), reps, prec)
+        d = np.abs(Knd.cpu().numpy() - Knd_o)
+        acc["near_dup"] = {"pairs": int(d.size), "K_range": [float(Knd_o.min()), float(Knd_o.max())],
+                           "max_abs_dK": float(d.max()), "mean_abs_dK": float(d.mean())}
+        line["accuracy_vs_oracle"] = acc
         # the FP64 path on the same GPU, on the first tiles of the same Gram (speedup report)
         if prec != "fp64":
-            nt = max(1, (te - tb) // 64)
+            nt = qsvm.qsvm_gram_num_tiles(N, reps, P) if args.full_fp64 else max(1, (te - tb) // 64)
             mps64 = torch.empty(qsvm.qsvm_mps_bytes(n, reps, N, 0), dtype=torch.uint8, device=dev)
             qsvm.qsvm_build_mps(Xd, reps, "fp64", mps=mps64)
             K64 = torch.full((N, N), float("nan"), dtype=torch.float64, device=dev)
@@ -314,10 +378,19 @@ def run_ours(args):
             sub_pairs = tiles_pairs(0, nt)
             fp64_rate = sub_pairs / (e0.elapsed_time(e1) * 1e-3)
             m = ~torch.isnan(K64)
+            dk = (K[m] - K64[m]).abs()
             line["fp64_same_gpu"] = {"entries_per_s": fp64_rate, "tiles_timed": nt,
                                      "speedup_of_" + prec: value / fp64_rate,
                                      "pair_kernel_speedup": (pairs_rank / (kms * 1e-3)) / fp64_rate,
-                                     "max_abs_dK_vs_fp64": float((K[m] - K64[m]).abs().max())}
+                                     "entries_compared": int(m.sum()),
+                                     "max_abs_dK_vs_fp64": float(dk.max()), "mean_abs_dK_vs_fp64": float(dk.mean())}
+            if Nte and args.full_fp64:
+                mte64 = qsvm.qsvm_build_mps(torch.from_numpy(Xte).to(dev), reps, "fp64")
+                Kx64, _ = qsvm.qsvm_kernel_cross(mte64, Nte, mps64, N, n, reps, "fp64")
+                dx = (Kx - Kx64).abs()
+                line["fp64_same_gpu"]["cross_max_abs_dK_vs_fp64"] = float(dx.max())
+                line["fp64_same_gpu"]["cross_mean_abs_dK_vs_fp64"] = float(dx.mean())
+                del Kx64, mte64
             del K64, mps64
         # CPU baseline: the oracle on the host cores, bounded sample
         rate, dt = cpu_oracle_rate(X, reps, args.cpu_pairs, 11)
@@ -356,6 +429,127 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """32 uneven Gram jobs (n from {16..784}, N in [64, 1024], reps = 2): one persistent
+    launch replayed from a CUDA graph, against per-job launches in the same precision
+    and per-job FP64 launches.  Single GPU: under torchrun only rank 0 runs."""
+    import torch
+
+    from paper_2405_02630_gb300 import build as qbuild
+    from paper_2405_02630_gb300 import qsvm
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    qbuild.build()
+    qsvm.lib()
+    reps, prec = 2, args.precision
+    P = qsvm.PRECISIONS[prec]
+    stream = torch.cuda.current_stream(dev)
+    spec = inputs.batch_jobs(seed=3)
+    Xs = [torch.from_numpy(X).to(dev) for X, _ in spec]
+
+    def make(pcode):
+        jobs = []
+        for (X, n), Xd in zip(spec, Xs):
+            N = X.shape[0]
+            jobs.append({"mps": torch.empty(qsvm.qsvm_mps_bytes(n, reps, N, pcode), dtype=torch.uint8, device=dev),
+                         "n_points": N, "n_qubits": n, "X": Xd,
+                         "K": torch.empty((N, N), dtype=torch.float64, device=dev), "logK": None})
+        return jobs
+
+    def build_all(jobs, pcode):
+        for j in jobs:
+            qsvm.qsvm_build_mps(j["X"], reps, pcode, mps=j["mps"], stream=stream)
+
+    jobs = make(P)
+    ws = torch.empty(qsvm.qsvm_batch_workspace_bytes(len(jobs)), dtype=torch.uint8, device=dev)
+    total_pairs = sum(j["n_points"] * (j["n_points"] + 1) // 2 for j in jobs)
+    algo_flops = sum(8.0 * structured_cmacs_per_entry(j["n_qubits"], reps) * j["n_points"] * (j["n_points"] + 1) / 2
+                     for j in jobs)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    build_all(jobs, P)
+    torch.cuda.synchronize()
+    plan = qsvm.qsvm_batch_plan_create(jobs, reps, prec, ws)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        tot, kern = [], []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            fn(em)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot.append(e0.elapsed_time(e1))
+            kern.append(em.elapsed_time(e1))
+        return sum(tot) / len(tot), sum(kern) / len(kern)
+
+    def step_batch(em=None):
+        build_all(jobs, P)
+        if em is not None:
+            em.record(stream)
+        plan.launch(stream)
+
+    def step_perjob(em=None):
+        build_all(jobs, P)
+        if em is not None:
+            em.record(stream)
+        for j in jobs:
+            qsvm.qsvm_kernel_gram(j["mps"], j["n_points"], j["n_qubits"], reps, prec, K=j["K"], stream=stream)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, kms = timed(step_batch, args.steps, args.warmup)
+    clocks = sampler.stop()
+    Kb = [j["K"].clone() for j in jobs]
+    ms_pj, kms_pj = timed(step_perjob, max(1, args.steps // 2), 1)
+    same = all(torch.equal(a, j["K"]) for a, j in zip(Kb, jobs))
+    jobs64 = make(0)
+
+    def step_fp64(em=None):
+        build_all(jobs64, 0)
+        if em is not None:
+            em.record(stream)
+        for j in jobs64:
+            qsvm.qsvm_kernel_gram(j["mps"], j["n_points"], j["n_qubits"], reps, "fp64", K=j["K"], stream=stream)
+
+    ms64, kms64 = timed(step_fp64, 1, 1)
+    dk = max(float((a - j["K"]).abs().max()) for a, j in zip(Kb, jobs64))
+    value = total_pairs / (ms * 1e-3)
+    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved = algo_flops / (kms * 1e-3) / 1e12
+    line = {
+        "metric": "gram_entries_per_s", "value": value, "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": {"fp32_split": "f32x2-split", "fp32": "f32", "fp64": "f64"}[prec],
+        "data": "synthetic",
+        "config": {"workload": "batch_cfg3", "jobs": len(jobs), "reps": reps, "precision": prec,
+                   "n_qubits": sorted({j["n_qubits"] for j in jobs}),
+                   "n_points_range": [min(j["n_points"] for j in jobs), max(j["n_points"] for j in jobs)],
+                   "entries": "unique pairs i<=j over all jobs", "launch": "persistent kernel replayed from a CUDA graph",
+                   "l2": "flushed (512 MB write) between timed steps"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": f"pair_persistent_kernel<chi=4,{prec}>"},
+        "gpu_launches": (len(jobs) + 1) * args.steps,
+        "clocks": clocks,
+        "contraction_ms": kms,
+        "per_job_launches": {"entries_per_s": total_pairs / (ms_pj * 1e-3), "contraction_ms": kms_pj,
+                             "bit_identical_to_batch": same},
+        "per_job_fp64": {"entries_per_s": total_pairs / (ms64 * 1e-3), "contraction_ms": kms64,
+                         "max_abs_dK_batch_vs_fp64": dk},
+    }
+    plan.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,9 +562,12 @@ def main():
     ap.add_argument("--ref-pairs", type=int, default=16384)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the accuracy, FP64 and CPU side measurements")
+    ap.add_argument("--full-fp64", action="store_true", help="compare every entry with the FP64 path (small N)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch_cfg3":
+        return run_batch(args)
     return run_ours(args)
 
 
