@@ -229,6 +229,11 @@ int32_t qsvm_autotune(const void* mps, int64_t n_points, int32_t n_qubits, int32
  * library's kernels on the current device: QSVM_OK or QSVM_ERR_TIMEOUT.
  * Synchronises `stream`.  Returns QSVM_OK or QSVM_ERR_CUDA. */
 int32_t qsvm_device_status(void* stream, int32_t clear, int32_t* status_out);
+/* Exercises the failure path without a fault: launches one CTA that waits on an
+ * mbarrier phase nothing completes, bounded by limit_ns (1e3 .. 2e9); the wait
+ * gives up, the kernel records QSVM_ERR_TIMEOUT in the status word (read it with
+ * qsvm_device_status) and returns, leaving the context usable. */
+int32_t qsvm_selftest_wait_timeout(int64_t limit_ns, void* stream);
 const char* qsvm_last_error(void);
 const char* qsvm_version(void);
 

@@ -13,12 +13,16 @@ struct PipeShape {
 };
 static const PipeShape kShapes[] = {{512, 4}, {1024, 3}, {512, 3}, {1024, 2}, {1024, 4}, {2048, 2}, {2048, 3}, {512, 2}};
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
-constexpr int kDefaultShape = 1;
+
+// Defaults from autotuner runs on one GB300 (n = 784 Grams): plain FP32 and the
+// chi = 8 kernels gain a resident CTA per SM with two stages; split FP32 at
+// chi <= 4 is fastest with three stages of 1 KB chunks.
+int default_shape(int chi, int prec) { return (prec == QSVM_FP32 || chi >= 8) ? 3 : 1; }
 
 int num_pipe_shapes() { return kNumShapes; }
 
 PipeCfg make_pipe(int chi, int prec, int shape) {
-  if (shape < 0 || shape >= kNumShapes) shape = kDefaultShape;
+  if (shape < 0 || shape >= kNumShapes) shape = default_shape(chi, prec);
   const int rec = (int)record_bytes(chi, prec);
   PipeCfg pc;
   pc.S = kShapes[shape].chunk_bytes >= rec ? kShapes[shape].chunk_bytes / rec : 1;
@@ -143,6 +147,30 @@ cudaError_t pair_status(cudaStream_t st, int clear, int32_t* out) {
   }
   *out = v;
   return e;
+}
+
+}  // namespace qsvm
+
+namespace qsvm {
+
+// Failure-path self test: one CTA waits on an mbarrier phase that nothing will
+// complete (no thread arrives, no copy is issued), with a caller-given bound.
+// The bounded wait gives up, the kernel records QSVM_ERR_TIMEOUT in the status
+// word exactly as a pair kernel does, and returns; the context stays usable.
+__global__ void wait_timeout_selftest_kernel(uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+  if (!ok && threadIdx.x == 0) atomicCAS(&g_pair_status, 0, (int32_t)QSVM_ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_timeout_selftest(uint64_t limit_ns, cudaStream_t st) {
+  wait_timeout_selftest_kernel<<<1, 32, 0, st>>>(limit_ns);
+  return cudaGetLastError();
 }
 
 }  // namespace qsvm

@@ -20,6 +20,7 @@ cudaError_t launch_persistent(int chi, int prec, const BatchArgs& a, const PipeC
 int pair_tile_dim(int chi, int prec);
 cudaError_t pair_status(cudaStream_t st, int clear, int32_t* out);
 int num_pipe_shapes();
+cudaError_t launch_wait_timeout_selftest(uint64_t limit_ns, cudaStream_t st);
 PipeCfg make_pipe(int chi, int prec, int shape);
 int pipe_smem(const PipeCfg& pc);
 }  // namespace qsvm
@@ -464,6 +465,14 @@ int32_t qsvm_device_status(void* stream, int32_t clear, int32_t* status_out) {
   cudaError_t e = pair_status(static_cast<cudaStream_t>(stream), clear, &v);
   if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
   *status_out = v;
+  return QSVM_OK;
+}
+
+int32_t qsvm_selftest_wait_timeout(int64_t limit_ns, void* stream) {
+  if (limit_ns < 1000 || limit_ns > 2000000000LL)
+    return fail(QSVM_ERR_ARG, "limit_ns=%lld outside [1e3, 2e9]", (long long)limit_ns);
+  cudaError_t e = launch_wait_timeout_selftest((uint64_t)limit_ns, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
   return QSVM_OK;
 }
 

@@ -73,6 +73,7 @@ _SIGS = {
     "qsvm_autotune": (_i32, [_vp, _i64, _i32, _i32, _i32, _dp, _i64, _vp, ctypes.POINTER(_i32),
                              ctypes.POINTER(ctypes.c_float)]),
     "qsvm_device_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
+    "qsvm_selftest_wait_timeout": (_i32, [_i64, _vp]),
     "qsvm_last_error": (ctypes.c_char_p, []),
     "qsvm_version": (ctypes.c_char_p, []),
 }
@@ -296,6 +297,10 @@ def qsvm_device_status(clear: bool = True, stream=None) -> int:
     v = _i32(0)
     _check(lib().qsvm_device_status(_stream(stream), 1 if clear else 0, ctypes.byref(v)))
     return int(v.value)
+
+
+def qsvm_selftest_wait_timeout(limit_ns: int, stream=None):
+    _check(lib().qsvm_selftest_wait_timeout(limit_ns, _stream(stream)))
 
 
 def qsvm_last_error() -> str:

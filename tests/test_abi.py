@@ -145,3 +145,12 @@ def test_configs():
 def test_autotune_buckets():
     from paper_2405_02630_gb300 import autotune
     assert [autotune.n_bucket(n) for n in (2, 16, 17, 784)] == [2, 16, 32, 1024]
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(qsvm, "LIB_PATH", str(tmp_path / "missing" / "libqsvm.so"))
+    monkeypatch.setattr(qsvm, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        qsvm.lib()
+    with pytest.raises(RuntimeError):
+        qsvm.qsvm_mps_bytes(8, 2, 4, "fp64")
