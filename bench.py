@@ -235,12 +235,13 @@ def run_ours(args):
 
     td = qsvm.qsvm_gram_tile_dim(reps, P)
 
-    def tiles_pairs(lo, hi):
-        # pairs contracted by tiles [lo, hi) of the Gram's tile order
+    def tiles_pairs(lo, hi, pcode=P):
+        # pairs contracted by tiles [lo, hi) of the Gram's tile order (tile size depends on the precision)
+        tdim = qsvm.qsvm_gram_tile_dim(reps, pcode)
         tot = 0
         for bb in range(lo, hi):
-            ti, tj = qsvm.qsvm_gram_tile_coords(N, reps, P, bb)
-            ni, nj = min(td, N - ti * td), min(td, N - tj * td)
+            ti, tj = qsvm.qsvm_gram_tile_coords(N, reps, pcode, bb)
+            ni, nj = min(tdim, N - ti * tdim), min(tdim, N - tj * tdim)
             tot += ni * (ni + 1) // 2 if ti == tj else ni * nj
         return tot
 
@@ -364,7 +365,8 @@ def run_ours(args):
         line["accuracy_vs_oracle"] = acc
         # the FP64 path on the same GPU, on the first tiles of the same Gram (speedup report)
         if prec != "fp64":
-            nt = qsvm.qsvm_gram_num_tiles(N, reps, P) if args.full_fp64 else max(1, (te - tb) // 64)
+            nt64 = qsvm.qsvm_gram_num_tiles(N, reps, 0)
+            nt = nt64 if args.full_fp64 else max(1, nt64 // 64)
             mps64 = torch.empty(qsvm.qsvm_mps_bytes(n, reps, N, 0), dtype=torch.uint8, device=dev)
             qsvm.qsvm_build_mps(Xd, reps, "fp64", mps=mps64)
             K64 = torch.full((N, N), float("nan"), dtype=torch.float64, device=dev)
@@ -375,7 +377,7 @@ def run_ours(args):
             qsvm.qsvm_kernel_gram_tiles(mps64, N, n, reps, "fp64", 0, nt, K64)
             e1.record()
             torch.cuda.synchronize()
-            sub_pairs = tiles_pairs(0, nt)
+            sub_pairs = tiles_pairs(0, nt, 0)
             fp64_rate = sub_pairs / (e0.elapsed_time(e1) * 1e-3)
             m = ~torch.isnan(K64)
             dk = (K[m] - K64[m]).abs()

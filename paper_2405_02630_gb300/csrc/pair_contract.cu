@@ -28,16 +28,16 @@ PipeCfg make_pipe(int chi, int prec, int shape) {
   pc.S = kShapes[shape].chunk_bytes >= rec ? kShapes[shape].chunk_bytes / rec : 1;
   pc.stages = kShapes[shape].stages;
   pc.slot_bytes = pc.S * rec + 16;
-  pc.stage_bytes = 2 * kTI * pc.slot_bytes;
+  pc.stage_bytes = 2 * tile_side(chi, prec) * pc.slot_bytes;
   return pc;
 }
 
-int pipe_smem(const PipeCfg& pc) { return pipe_smem_bytes(pc); }
+int pipe_smem(const PipeCfg& pc, int chi, int prec) { return pipe_smem_bytes(pc, chi, prec); }
 
 template <int CHI, int PREC>
 static cudaError_t launch_pair_t(const TileArgs& a, int64_t ntiles, const PipeCfg& pc, cudaStream_t st) {
   auto kern = pair_tile_kernel<CHI, PREC>;
-  const int smem = pipe_smem_bytes(pc);
+  const int smem = pipe_smem_bytes(pc, CHI, PREC);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int64_t done = 0;
@@ -59,7 +59,7 @@ static cudaError_t launch_pair_t(const TileArgs& a, int64_t ntiles, const PipeCf
 template <int CHI, int PREC>
 static cudaError_t prepare_persistent_t(const PipeCfg& pc, int64_t total_tiles, int* grid_out) {
   auto kern = pair_persistent_kernel<CHI, PREC>;
-  const int smem = pipe_smem_bytes(pc);
+  const int smem = pipe_smem_bytes(pc, CHI, PREC);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -75,7 +75,7 @@ static cudaError_t prepare_persistent_t(const PipeCfg& pc, int64_t total_tiles, 
 
 template <int CHI, int PREC>
 static cudaError_t launch_persistent_t(const BatchArgs& a, const PipeCfg& pc, int grid, cudaStream_t st) {
-  pair_persistent_kernel<CHI, PREC><<<(unsigned)grid, kTileThreads, pipe_smem_bytes(pc), st>>>(a, pc);
+  pair_persistent_kernel<CHI, PREC><<<(unsigned)grid, kTileThreads, pipe_smem_bytes(pc, CHI, PREC), st>>>(a, pc);
   return cudaGetLastError();
 }
 
@@ -130,11 +130,7 @@ cudaError_t launch_persistent(int chi, int prec, const BatchArgs& a, const PipeC
   }
 }
 
-int pair_tile_dim(int chi, int prec) {
-  (void)chi;
-  (void)prec;
-  return kTI;
-}
+int pair_tile_dim(int chi, int prec) { return tile_side(chi, prec); }
 
 cudaError_t pair_status(cudaStream_t st, int clear, int32_t* out) {
   int32_t v = 0;

@@ -450,16 +450,202 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
 // Device status word of this translation unit (QSVM_OK or QSVM_ERR_TIMEOUT).
 __device__ int32_t g_pair_status;
 
-constexpr int kTI = 16;               // a tile is kTI x kTI pairs, one per thread
-constexpr int kTileThreads = kTI * kTI;
+// Split FP32 at chi = 8 with four threads per pair.  One thread cannot hold a
+// pair's split environment (2 blocks x 16 entries x hi/lo/full = 192 floats) in
+// registers, so thread (s, h) of a quad owns rows {2h, 2h+1} of block s of the
+// new environment.  Per site it reads the whole old environment from a padded
+// shared buffer (every row is needed: X[p][r] = sum_q a[q][p] E_c[q][r]), builds
+// its two rows of X_cs for c = 0, 1, accumulates its two rows of
+// E'_s = sum_c X_cs conj(b_cs), and after a warp barrier writes them back.  The
+// quad agrees on the power-of-two rescale through two xor-shuffles.  The
+// arithmetic per entry is exactly that of Engine<8, QSVM_FP32_SPLIT>: the same
+// grids, the same three products per real MAC.
+template <int PREC>
+struct QuadEngine;
+
+template <>
+struct QuadEngine<QSVM_FP32_SPLIT> {
+  static constexpr int CHI = 8, H = 4;
+  static constexpr int GX = grid_x(CHI);
+  static constexpr int kRenormEvery = 1;
+  using Rec = Record<CHI, QSVM_FP32_SPLIT>;
+  float* ebuf;     // this pair's environment: entry (c, q, r) at (c*16 + q*4 + r) * 4 floats: hi.re, hi.im, lo.re, lo.im
+  int s, h;        // block of E' and row pair this thread owns
+  unsigned mask;   // the warp's active mask (all 32 lanes run the site loop together)
+  int L;
+
+  __device__ __forceinline__ void init(float* pair_buf, int quarter) {
+    ebuf = pair_buf;
+    s = quarter >> 1;
+    h = quarter & 1;
+    mask = 0xffffffffu;
+    L = 0;
+    // E_0 = e_0 e_0^T: entry (c=0, q=0, r=0) = 1, all else 0; each thread clears its own rows
+    for (int p = 0; p < 2; ++p)
+      for (int r = 0; r < H; ++r) {
+        const int q = 2 * h + p;
+        float4* e = reinterpret_cast<float4*>(ebuf + (s * 16 + q * 4 + r) * 4);
+        *e = make_float4((s == 0 && q == 0 && r == 0) ? 1.f : 0.f, 0.f, 0.f, 0.f);
+      }
+    __syncwarp(mask);
+  }
+
+  __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 Nh[2][H], Nl[2][H];  // own rows p = 2h + {0, 1} of E'_s
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int pp = 0; pp < H; ++pp) Nh[p][pp] = Nl[p][pp] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const uint32_t pa = ra + (2 * c + s) * Rec::kBlockBytes;
+      const uint32_t pb = rb + (2 * c + s) * Rec::kBlockBytes;
+      // step 1: X[p][r] = sum_q a[q][p] E_c[q][r] for the thread's two rows p
+      float2 Xh[2][H], Xl[2][H], Xf[2][H];
+      {
+        float2 hh[2][H], ll[2][H];
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int r = 0; r < H; ++r) hh[p][r] = ll[p][r] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < H; ++q) {
+          float2 Ah[2], iAh[2], Al[2], iAl[2];
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            const float4* fa = reinterpret_cast<const float4*>(sptr(pa + (q * H + 2 * h + p) * 16));
+            const float4* fl = reinterpret_cast<const float4*>(sptr(pa + Rec::kPartBytes + (q * H + 2 * h + p) * 16));
+            const float4 va = fa[0], vl = fl[0];
+            Ah[p] = make_float2(va.x, va.y);
+            iAh[p] = make_float2(va.z, va.w);
+            Al[p] = make_float2(vl.x, vl.y);
+            iAl[p] = make_float2(vl.z, vl.w);
+          }
+#pragma unroll
+          for (int r = 0; r < H; ++r) {
+            const float4 ev = *reinterpret_cast<const float4*>(ebuf + (c * 16 + q * 4 + r) * 4);
+            const float2 e = make_float2(ev.x, ev.y), el = make_float2(ev.z, ev.w);
+            const float2 ef = add2(e, el);
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+              hh[p][r] = fma2(bc(e.x), Ah[p], hh[p][r]);
+              hh[p][r] = fma2(bc(e.y), iAh[p], hh[p][r]);
+              ll[p][r] = fma2(bc(el.x), Ah[p], ll[p][r]);
+              ll[p][r] = fma2(bc(el.y), iAh[p], ll[p][r]);
+              ll[p][r] = fma2(bc(ef.x), Al[p], ll[p][r]);
+              ll[p][r] = fma2(bc(ef.y), iAl[p], ll[p][r]);
+            }
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int r = 0; r < H; ++r) {
+            const float2 v = add2(hh[p][r], ll[p][r]);
+            const float2 xh = grid_round2<GX>(v);
+            Xh[p][r] = xh;
+            Xl[p][r] = add2(fma2(xh, m1, hh[p][r]), ll[p][r]);
+            Xf[p][r] = v;
+          }
+      }
+      // step 2: N[p][pp] += sum_r X[p][r] conj(b[r][pp])
+#pragma unroll
+      for (int r = 0; r < H; ++r) {
+#pragma unroll
+        for (int pp = 0; pp < H; ++pp) {
+          const float4 vb = reinterpret_cast<const float4*>(sptr(pb + (r * H + pp) * 16))[0];
+          const float4 vl = reinterpret_cast<const float4*>(sptr(pb + Rec::kPartBytes + (r * H + pp) * 16))[0];
+          const float2 Bh = make_float2(vb.x, vb.y), iBh = make_float2(vb.z, vb.w);
+          const float2 Bl = make_float2(vl.x, vl.y), iBl = make_float2(vl.z, vl.w);
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            Nh[p][pp] = fma2(bc(Xh[p][r].x), Bh, Nh[p][pp]);
+            Nh[p][pp] = fma2(bc(Xh[p][r].y), iBh, Nh[p][pp]);
+            Nl[p][pp] = fma2(bc(Xf[p][r].x), Bl, Nl[p][pp]);
+            Nl[p][pp] = fma2(bc(Xf[p][r].y), iBl, Nl[p][pp]);
+            Nl[p][pp] = fma2(bc(Xl[p][r].x), Bh, Nl[p][pp]);
+            Nl[p][pp] = fma2(bc(Xl[p][r].y), iBh, Nl[p][pp]);
+          }
+        }
+      }
+    }
+    // quad-wide rescale by 2^-e, then split onto the E grid
+    float2 V[2][H];
+    float m = 0.f;
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int pp = 0; pp < H; ++pp) {
+        V[p][pp] = add2(Nh[p][pp], Nl[p][pp]);
+        m = fmaxf(m, fmaxf(fabsf(V[p][pp].x), fabsf(V[p][pp].y)));
+      }
+    m = fmaxf(m, __shfl_xor_sync(mask, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(mask, m, 2));
+    int e = 0;
+    if (m > 0.f && isfinite(m)) {
+      frexpf(m, &e);
+      if (e < -120) {
+        const float2 up = bc(pow2f(100));
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int pp = 0; pp < H; ++pp) {
+            Nh[p][pp] = mul2(Nh[p][pp], up);
+            Nl[p][pp] = mul2(Nl[p][pp], up);
+            V[p][pp] = mul2(V[p][pp], up);
+          }
+        L -= 100;
+        e += 100;
+      }
+    }
+    const float2 sc = bc(pow2f(-e));
+    __syncwarp(mask);  // every thread of the warp has read the old environment
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int pp = 0; pp < H; ++pp) {
+        const float2 f = mul2(V[p][pp], sc);
+        const float2 hv = grid_round2<kGridE>(f);
+        const float2 lv = fma2(Nl[p][pp], sc, fma2(hv, m1, mul2(Nh[p][pp], sc)));
+        *reinterpret_cast<float4*>(ebuf + (s * 16 + (2 * h + p) * 4 + pp) * 4) = make_float4(hv.x, hv.y, lv.x, lv.y);
+      }
+    __syncwarp(mask);  // the new environment is complete before anyone reads it
+    L += e;
+  }
+
+  __device__ __forceinline__ void renorm() {}
+
+  // amplitude = E_0[0][0] + E_1[0][0] (both in the shared buffer after the last site)
+  __device__ __forceinline__ void amplitude(double& re, double& im) const {
+    const float4 a = *reinterpret_cast<const float4*>(ebuf + (0 * 16 + 0) * 4);
+    const float4 b = *reinterpret_cast<const float4*>(ebuf + (1 * 16 + 0) * 4);
+    re = ((double)a.x + (double)a.z) + ((double)b.x + (double)b.z);
+    im = ((double)a.y + (double)a.w) + ((double)b.y + (double)b.w);
+  }
+};
+
+constexpr int kTileThreads = 256;      // every tile kernel runs 256 threads
 constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kMaxStages = 4;
-constexpr int kOutBytes = kTI * (kTI + 1) * 16;
 constexpr int kCtlBytes = 128;
+
+// Tile geometry: one thread per pair on a 16 x 16 tile, except split FP32 at
+// chi = 8, which runs four threads per pair on an 8 x 8 tile (QuadEngine).
+__host__ __device__ constexpr int threads_per_pair(int chi, int prec) {
+  return (chi >= 8 && prec == QSVM_FP32_SPLIT) ? 4 : 1;
+}
+__host__ __device__ constexpr int tile_side(int chi, int prec) { return threads_per_pair(chi, prec) == 4 ? 8 : 16; }
+__host__ __device__ constexpr int out_bytes(int ti) { return ti * (ti + 1) * 16; }
+// shared environment buffer of the four-thread layout: 32 entries x 16 B per pair, +16 B
+constexpr int kQuadPairFloats = 32 * 4 + 4;
+__host__ __device__ constexpr int ebuf_bytes(int chi, int prec) {
+  return threads_per_pair(chi, prec) == 4 ? (kTileThreads / 4) * kQuadPairFloats * 4 : 0;
+}
 
 template <int CHI, int PREC>
 __host__ __device__ constexpr int min_blocks_per_sm() {
-  return (CHI >= 8) ? 1 : ((PREC == QSVM_FP32) ? 3 : 2);
+  return (threads_per_pair(CHI, PREC) == 4) ? 2 : (CHI >= 8) ? 1 : ((PREC == QSVM_FP32) ? 3 : 2);
 }
 
 // Shared-memory control block at the end of the dynamic allocation.
@@ -472,7 +658,10 @@ struct TileCtl {
 };
 static_assert(sizeof(TileCtl) <= kCtlBytes, "control block");
 
-__host__ __device__ inline int pipe_smem_bytes(const PipeCfg& pc) { return pc.stages * pc.stage_bytes + kOutBytes + kCtlBytes; }
+// Dynamic shared memory: stages | output tile (K, logK) | control block | environment buffer (4-thread layout)
+__host__ __device__ inline int pipe_smem_bytes(const PipeCfg& pc, int chi, int prec) {
+  return pc.stages * pc.stage_bytes + out_bytes(tile_side(chi, prec)) + kCtlBytes + ebuf_bytes(chi, prec);
+}
 
 // What one tile needs to know.
 struct TileWork {
@@ -495,11 +684,22 @@ struct TileWork {
 // of the chunk pc.stages ahead into that stage; warps only wait for data.
 // gchunk is the CTA's running chunk count (stage and mbarrier parity continue
 // across the tiles a persistent CTA processes).  Returns false after a timeout.
+template <int CHI, int PREC, int TPP>
+struct EngineFor {
+  using type = Engine<CHI, PREC>;
+};
+template <int CHI, int PREC>
+struct EngineFor<CHI, PREC, 4> {
+  using type = QuadEngine<PREC>;
+};
+
 template <int CHI, int PREC>
 __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, uint8_t* smem, TileCtl* ctl,
                                          int& gchunk) {
   using Rec = Record<CHI, PREC>;
-  constexpr int TI = kTI;
+  constexpr int TPP = threads_per_pair(CHI, PREC);
+  constexpr int TI = tile_side(CHI, PREC);
+  using Eng = typename EngineFor<CHI, PREC, TPP>::type;
   const int S = pc.S, NST = pc.stages, SLOT = pc.slot_bytes, STAGE = pc.stage_bytes;
   double* outK = reinterpret_cast<double*>(smem + NST * STAGE);
   double* outL = outK + TI * (TI + 1);
@@ -510,7 +710,8 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
   const int n = w.n;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int ty = tid / TI, tx = tid % TI;
+  const int pair = tid / TPP, quarter = tid % TPP;
+  const int ty = pair / TI, tx = pair % TI;
   const bool diag_tile = w.symmetric && w.ti == w.tj;
   const bool valid = ty < ni && tx < nj && (!diag_tile || ty <= tx);
   const int slotA = min(ty, ni - 1);
@@ -537,8 +738,13 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
     for (int ch = 0; ch < min(NST, nchunks); ++ch) issue(ch);
   __syncthreads();
 
-  Engine<CHI, PREC> eng;
-  eng.init();
+  Eng eng;
+  if constexpr (TPP == 4) {
+    float* ebuf = reinterpret_cast<float*>(smem + NST * STAGE + out_bytes(TI) + kCtlBytes) + pair * kQuadPairFloats;
+    eng.init(ebuf, quarter);
+  } else {
+    eng.init();
+  }
   for (int ch = 0; ch < nchunks; ++ch) {
     const int g = g0 + ch;
     const int st = g % NST;
@@ -559,14 +765,16 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
     const uint32_t base = smem_u32(smem) + st * STAGE;
     const int k0 = ch * S;
     const int ns = min(S, n - k0);
-    if (valid) {
+    // the four-thread layout synchronises the warp inside site(), so every pair of
+    // such a tile computes (on clamped points if it is outside the tile) and only
+    // valid pairs write results
+    if (valid || TPP > 1) {
       const uint32_t pa = base + slotA * SLOT;
       const uint32_t pb = base + slotB * SLOT;
 #pragma unroll 1
       for (int s = 0; s < ns; ++s) {
         eng.site(pa + s * Rec::kBytes, pb + s * Rec::kBytes);
-        if (Engine<CHI, PREC>::kRenormEvery > 1 && ((k0 + s + 1) % Engine<CHI, PREC>::kRenormEvery) == 0)
-          eng.renorm();
+        if (Eng::kRenormEvery > 1 && ((k0 + s + 1) % Eng::kRenormEvery) == 0) eng.renorm();
       }
     }
     __syncwarp();
@@ -600,8 +808,9 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
   }
 
   double kval = 0.0, lval = -INFINITY;
-  if (valid) {
-    if (Engine<CHI, PREC>::kRenormEvery > 1) eng.renorm();
+  const bool writer = valid && quarter == 0;
+  if (writer) {
+    if (Eng::kRenormEvery > 1) eng.renorm();
     double re, im;
     eng.amplitude(re, im);
     const double a2 = re * re + im * im;
@@ -615,11 +824,13 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
   if (w.symmetric) {
     // mirror K[j][i] = K[i][j] bit-exactly, through shared memory so that the
     // transposed rows are written contiguously
-    outK[ty * (TI + 1) + tx] = kval;
-    outL[ty * (TI + 1) + tx] = lval;
+    if (quarter == 0) {
+      outK[ty * (TI + 1) + tx] = kval;
+      outL[ty * (TI + 1) + tx] = lval;
+    }
     __syncthreads();
     // this thread writes row j0+ty, column i0+tx: the value of pair (i0+tx, j0+ty)
-    const bool src = tx < ni && ty < nj && (!diag_tile || tx < ty);
+    const bool src = quarter == 0 && tx < ni && ty < nj && (!diag_tile || tx < ty);
     if (src) {
       w.K[(j0 + ty) * w.ldk + (i0 + tx)] = outK[tx * (TI + 1) + ty];
       if (w.logK) w.logK[(j0 + ty) * w.ldl + (i0 + tx)] = outL[tx * (TI + 1) + ty];
@@ -629,8 +840,9 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
   return true;
 }
 
+template <int CHI, int PREC>
 __device__ __forceinline__ TileCtl* tile_ctl(uint8_t* smem, const PipeCfg& pc) {
-  return reinterpret_cast<TileCtl*>(smem + pc.stages * pc.stage_bytes + kOutBytes);
+  return reinterpret_cast<TileCtl*>(smem + pc.stages * pc.stage_bytes + out_bytes(tile_side(CHI, PREC)));
 }
 
 __device__ __forceinline__ void tile_ctl_init(TileCtl* ctl, const PipeCfg& pc) {
@@ -651,7 +863,7 @@ template <int CHI, int PREC>
 __global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>()))
     pair_tile_kernel(TileArgs args, PipeCfg pc) {
   uint8_t* smem = qsvm_dyn_smem;
-  TileCtl* ctl = tile_ctl(smem, pc);
+  TileCtl* ctl = tile_ctl<CHI, PREC>(smem, pc);
   tile_ctl_init(ctl, pc);
   const int64_t b = args.tile_begin + blockIdx.x;
   TileWork w;
@@ -679,7 +891,7 @@ template <int CHI, int PREC>
 __global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>()))
     pair_persistent_kernel(BatchArgs args, PipeCfg pc) {
   uint8_t* smem = qsvm_dyn_smem;
-  TileCtl* ctl = tile_ctl(smem, pc);
+  TileCtl* ctl = tile_ctl<CHI, PREC>(smem, pc);
   tile_ctl_init(ctl, pc);
   int gchunk = 0;
   while (true) {

@@ -22,7 +22,7 @@ cudaError_t pair_status(cudaStream_t st, int clear, int32_t* out);
 int num_pipe_shapes();
 cudaError_t launch_wait_timeout_selftest(uint64_t limit_ns, cudaStream_t st);
 PipeCfg make_pipe(int chi, int prec, int shape);
-int pipe_smem(const PipeCfg& pc);
+int pipe_smem(const PipeCfg& pc, int chi, int prec);
 }  // namespace qsvm
 
 using namespace qsvm;
@@ -404,7 +404,7 @@ int32_t qsvm_set_config(int32_t reps, int32_t precision, int32_t index) {
   int32_t rc = check_common(2, reps, precision);
   if (rc) return rc;
   if (index < -1 || index >= num_pipe_shapes()) return fail(QSVM_ERR_ARG, "config index %d out of range", index);
-  if (index >= 0 && pipe_smem(make_pipe(1 << reps, precision, index)) > kMaxSmemPerCta)
+  if (index >= 0 && pipe_smem(make_pipe(1 << reps, precision, index), 1 << reps, precision) > kMaxSmemPerCta)
     return fail(QSVM_ERR_ARG, "config %d needs more shared memory than a CTA has", index);
   g_config[reps - 1][precision].store(index);
   return QSVM_OK;
@@ -431,7 +431,7 @@ int32_t qsvm_autotune(const void* mps, int64_t n_points, int32_t n_qubits, int32
   int32_t out = QSVM_OK;
   for (int c = 0; c < num_pipe_shapes() && out == QSVM_OK; ++c) {
     float ms = -1.f;
-    if (pipe_smem(make_pipe(1 << reps, precision, c)) <= kMaxSmemPerCta) {
+    if (pipe_smem(make_pipe(1 << reps, precision, c), 1 << reps, precision) <= kMaxSmemPerCta) {
       g_config[reps - 1][precision].store(c);
       // one untimed run, then the timed one
       for (int it = 0; it < 2 && out == QSVM_OK; ++it) {
