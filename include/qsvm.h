@@ -224,6 +224,20 @@ int32_t qsvm_get_config(int32_t reps, int32_t precision);
 int32_t qsvm_autotune(const void* mps, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
                       double* K, int64_t ldk, void* stream, int32_t* best_out, float* ms_out);
 
+/* ---- state-vector validator (small n) --------------------------------------
+ * The state-vector recipe of Algorithm 1 on the GPU: every point's circuit is
+ * simulated gate by gate (literal H, RZ, CNOT) on its 2^n complex128 amplitudes,
+ * then K[i][j] = |<psi_j|psi_i>|^2 (Eq. 3-4) is formed from inner products over
+ * the amplitudes in FP64.  It shares no code with the MPS builder or the pair
+ * kernels, so it cross-checks them; cost grows as 2^n (n_qubits <= 24).
+ *   X    device, n_points x n_qubits float64;  K device, n_points rows, ldk >= n_points
+ *        (symmetric, diagonal computed);  ws device scratch of at least
+ *        qsvm_sv_workspace_bytes() bytes (the state vectors).  reps is 1..64.
+ * Errors: QSVM_ERR_ARG, QSVM_ERR_WORKSPACE, QSVM_ERR_CUDA. */
+size_t qsvm_sv_workspace_bytes(int64_t n_points, int32_t n_qubits);
+int32_t qsvm_sv_gram(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, double* K, int64_t ldk,
+                     void* ws, size_t ws_bytes, void* stream);
+
 /* ---- diagnostics --------------------------------------------------------- */
 /* Reads (and, if clear != 0, resets) the device status words written by this
  * library's kernels on the current device: QSVM_OK or QSVM_ERR_TIMEOUT.

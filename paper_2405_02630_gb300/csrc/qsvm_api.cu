@@ -21,6 +21,8 @@ int pair_tile_dim(int chi, int prec);
 cudaError_t pair_status(cudaStream_t st, int clear, int32_t* out);
 int num_pipe_shapes();
 cudaError_t launch_wait_timeout_selftest(uint64_t limit_ns, cudaStream_t st);
+cudaError_t launch_sv_gram(const double* X, int64_t N, int n, int reps, void* ws, double* K, int64_t ldk,
+                           cudaStream_t st);
 PipeCfg make_pipe(int chi, int prec, int shape);
 int pipe_smem(const PipeCfg& pc, int chi, int prec);
 }  // namespace qsvm
@@ -465,6 +467,26 @@ int32_t qsvm_device_status(void* stream, int32_t clear, int32_t* status_out) {
   cudaError_t e = pair_status(static_cast<cudaStream_t>(stream), clear, &v);
   if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
   *status_out = v;
+  return QSVM_OK;
+}
+
+size_t qsvm_sv_workspace_bytes(int64_t n_points, int32_t n_qubits) {
+  if (n_points < 1 || n_qubits < 1 || n_qubits > 24) return 0;
+  return (size_t)n_points * ((size_t)1 << n_qubits) * 16;
+}
+
+int32_t qsvm_sv_gram(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, double* K, int64_t ldk,
+                     void* ws, size_t ws_bytes, void* stream) {
+  if (n_qubits < 1 || n_qubits > 24) return fail(QSVM_ERR_ARG, "n_qubits=%d outside 1..24 for state vectors", n_qubits);
+  if (reps < 1 || reps > 64) return fail(QSVM_ERR_ARG, "reps=%d outside 1..64", reps);
+  if (n_points < 1) return fail(QSVM_ERR_ARG, "n_points=%lld must be >= 1", (long long)n_points);
+  if (!X || !aligned(X, 8)) return fail(QSVM_ERR_ARG, "X must be a non-null 8-byte aligned device pointer");
+  if (!K || !aligned(K, 8) || ldk < n_points) return fail(QSVM_ERR_ARG, "K must be 8-byte aligned with ldk >= n_points");
+  if (!ws || !aligned(ws, 16)) return fail(QSVM_ERR_ARG, "ws must be a non-null 16-byte aligned device pointer");
+  const size_t need = qsvm_sv_workspace_bytes(n_points, n_qubits);
+  if (ws_bytes < need) return fail(QSVM_ERR_WORKSPACE, "ws_bytes=%zu < required %zu", ws_bytes, need);
+  cudaError_t e = launch_sv_gram(X, n_points, n_qubits, reps, ws, K, ldk, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "state-vector launch");
   return QSVM_OK;
 }
 

@@ -74,6 +74,8 @@ _SIGS = {
                              ctypes.POINTER(ctypes.c_float)]),
     "qsvm_device_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
     "qsvm_selftest_wait_timeout": (_i32, [_i64, _vp]),
+    "qsvm_sv_workspace_bytes": (_sz, [_i64, _i32]),
+    "qsvm_sv_gram": (_i32, [_dp, _i64, _i32, _i32, _dp, _i64, _vp, _sz, _vp]),
     "qsvm_last_error": (ctypes.c_char_p, []),
     "qsvm_version": (ctypes.c_char_p, []),
 }
@@ -297,6 +299,22 @@ def qsvm_device_status(clear: bool = True, stream=None) -> int:
     v = _i32(0)
     _check(lib().qsvm_device_status(_stream(stream), 1 if clear else 0, ctypes.byref(v)))
     return int(v.value)
+
+
+def qsvm_sv_workspace_bytes(n_points: int, n_qubits: int) -> int:
+    return int(lib().qsvm_sv_workspace_bytes(n_points, n_qubits))
+
+
+def qsvm_sv_gram(X, reps: int, K=None, ws=None, stream=None):
+    """State-vector Gram (Algorithm 1 recipe on the GPU) of the rows of X (small n)."""
+    import torch
+    N, n = X.shape
+    if K is None:
+        K = torch.empty((N, N), dtype=torch.float64, device=X.device)
+    if ws is None:
+        ws = torch.empty(max(16, qsvm_sv_workspace_bytes(N, n)), dtype=torch.uint8, device=X.device)
+    _check(lib().qsvm_sv_gram(_ptr(X), N, n, reps, _ptr(K), K.stride(0), _ptr(ws), ws.numel(), _stream(stream)))
+    return K
 
 
 def qsvm_selftest_wait_timeout(limit_ns: int, stream=None):

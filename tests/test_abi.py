@@ -154,3 +154,14 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
         qsvm.lib()
     with pytest.raises(RuntimeError):
         qsvm.qsvm_mps_bytes(8, 2, 4, "fp64")
+
+
+def test_statevector_sizes_and_errors():
+    assert qsvm.qsvm_sv_workspace_bytes(10, 8) == 10 * 256 * 16
+    assert qsvm.qsvm_sv_workspace_bytes(10, 25) == 0
+    L = qsvm.lib()
+    v = ctypes.c_void_p
+    assert L.qsvm_sv_gram(v(64), 4, 25, 2, v(64), 4, v(64), 1 << 30, None) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_sv_gram(v(64), 4, 8, 0, v(64), 4, v(64), 1 << 30, None) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_sv_gram(v(64), 4, 8, 2, v(64), 3, v(64), 1 << 30, None) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_sv_gram(v(64), 4, 8, 2, v(64), 4, v(64), 100, None) == qsvm.QSVM_ERR_WORKSPACE
