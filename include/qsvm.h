@@ -238,6 +238,32 @@ size_t qsvm_sv_workspace_bytes(int64_t n_points, int32_t n_qubits);
 int32_t qsvm_sv_gram(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, double* K, int64_t ldk,
                      void* ws, size_t ws_bytes, void* stream);
 
+/* ---- the support vector classifier on the kernel -----------------------------
+ * Sec. 3.2 / Sec. 4.2 hand the quantum kernel matrix to an SVC (primal Eq. 1-2,
+ * solved in its dual with the kernel in place of the inner product).  A binary
+ * problem selects its n training points from a symmetric kernel matrix K by idx
+ * and carries labels y = +1 / -1; qsvm_svc_fit solves the C-SVC dual
+ *   min 1/2 a^T Q a - 1^T a,  Q_ij = y_i y_j K[idx_i][idx_j],  0 <= a <= C,  y^T a = 0
+ * by sequential minimal optimisation with the maximal violating pair, stopping
+ * when the optimality gap is below tol or after max_iter steps; one CTA per
+ * problem, so all one-vs-one pairs of a multiclass fit share a launch.
+ * b_out[p] (device) gets the bias and iters_out[p] (device) the steps taken.
+ * qsvm_svc_decision writes F[r * n_problems + p] = sum_i a_i y_i Kx[r][idx_i] + b[p]
+ * for m rows of a test x train kernel Kx.  ws: device scratch (256-byte aligned)
+ * of qsvm_svc_workspace_bytes(problems) bytes (problem table and gradients). */
+typedef struct qsvm_svc_problem {
+  const int64_t* idx;  /* device, n row indices into K                            */
+  const int8_t* y;     /* device, n labels +1 / -1                                */
+  int64_t n;           /* >= 2                                                   */
+  double* alpha;       /* device output, n dual coefficients                     */
+} qsvm_svc_problem;
+size_t qsvm_svc_workspace_bytes(const qsvm_svc_problem* problems, int32_t n_problems);
+int32_t qsvm_svc_fit(const double* K, int64_t ldk, const qsvm_svc_problem* problems, int32_t n_problems, double C,
+                     double tol, int64_t max_iter, double* b_out, int64_t* iters_out, void* ws, size_t ws_bytes,
+                     void* stream);
+int32_t qsvm_svc_decision(const double* Kx, int64_t ldk, int64_t m, const qsvm_svc_problem* problems,
+                          int32_t n_problems, const double* b, double* F, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- diagnostics --------------------------------------------------------- */
 /* Reads (and, if clear != 0, resets) the device status words written by this
  * library's kernels on the current device: QSVM_OK or QSVM_ERR_TIMEOUT.

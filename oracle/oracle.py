@@ -72,6 +72,13 @@ def lib():
             L.qo_mps_cross.restype = c_int
             L.qo_mps_pairs.argtypes = [dp, dp, i64p, i64p, i64, c_int, c_int, c_int, dp, dp, c_int]
             L.qo_mps_pairs.restype = c_int
+            i8p = ctypes.POINTER(ctypes.c_byte)
+            L.qo_svc_fit.argtypes = [dp, ctypes.c_longlong, i64p, i8p, ctypes.c_longlong, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_longlong, dp, dp]
+            L.qo_svc_fit.restype = ctypes.c_longlong
+            L.qo_svc_decision.argtypes = [dp, ctypes.c_longlong, i64p, ctypes.c_longlong, dp, i8p, ctypes.c_double,
+                                          ctypes.c_longlong, dp]
+            L.qo_svc_decision.restype = None
             L.qo_max_threads.argtypes = []
             L.qo_max_threads.restype = c_int
             _lib = L
@@ -192,3 +199,37 @@ def mps_pairs(Xa, Xb, ia, ib, reps: int, flags: int = 0, threads: int = 0):
     if rc != 0:
         raise ValueError(f"qo_mps_pairs failed ({rc})")
     return K, LK
+
+
+# ----------------------------------------------------------------- SVC ---
+def svc_fit(K, y, C: float = 1.0, tol: float = 1e-8, max_iter: int = 1_000_000, idx=None):
+    """Binary C-SVC dual on a precomputed kernel by SMO (maximal violating pair).
+    Returns (alpha, b, iterations)."""
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.int8)
+    n = y.shape[0] if idx is None else len(idx)
+    ip = None
+    if idx is not None:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        ip = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    alpha = np.zeros(n)
+    b = np.zeros(1)
+    it = lib().qo_svc_fit(_dp(K), K.shape[1], ip, y.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)), n, C, tol,
+                          max_iter, _dp(alpha), _dp(b))
+    if it < 0:
+        raise ValueError("qo_svc_fit failed")
+    return alpha, float(b[0]), int(it)
+
+
+def svc_decision(Kx, alpha, y, b: float, idx=None):
+    Kx = np.ascontiguousarray(Kx, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.int8)
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    ip = None
+    if idx is not None:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        ip = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    f = np.zeros(Kx.shape[0])
+    lib().qo_svc_decision(_dp(Kx), Kx.shape[1], ip, Kx.shape[0], _dp(alpha),
+                          y.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)), b, alpha.shape[0], _dp(f))
+    return f

@@ -401,3 +401,76 @@ int qo_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ----------------------------------------------------------------- SVC --- */
+/* Binary C-SVC on a precomputed kernel (the support vector classifier trained on
+ * the quantum kernel matrix, Sec. 3.2 / Sec. 4.2; primal of Eq. 1-2 with the
+ * kernel in place of the inner product).  Dual: minimise
+ *   f(a) = 1/2 sum_ij a_i a_j y_i y_j K_ij - sum_i a_i,  0 <= a_i <= C, sum_i y_i a_i = 0,
+ * by sequential minimal optimisation: each step takes the maximal violating pair
+ *   i = argmax_{t in I_up} -y_t g_t,  j = argmin_{t in I_low} -y_t g_t
+ * (g = gradient, I_up = {a_t < C, y_t = +1} u {a_t > 0, y_t = -1}, I_low the mirror),
+ * stops when m(a) - M(a) < tol, and solves the two-variable subproblem exactly
+ * with clipping to the box.  K is row-major with leading dimension ldk; idx
+ * (nullable) selects the training points of K.  Returns iterations (< 0: error);
+ * b is the bias of f(x) = sum_i a_i y_i K(x, x_i) + b. */
+long long qo_svc_fit(const double* K, long long ldk, const long long* idx, const signed char* y, long long n,
+                     double C, double tol, long long max_iter, double* alpha, double* b_out) {
+  double* g = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!g) return -2;
+  for (long long t = 0; t < n; ++t) {
+    alpha[t] = 0.0;
+    g[t] = -1.0;
+  }
+#define KK(a, c) K[(idx ? idx[a] : (a)) * ldk + (idx ? idx[c] : (c))]
+  long long it = 0;
+  double m = 0.0, M = 0.0;
+  for (; it < max_iter; ++it) {
+    long long i = -1, j = -1;
+    m = -INFINITY;
+    M = INFINITY;
+    for (long long t = 0; t < n; ++t) {
+      const double v = -y[t] * g[t];
+      const int up = (y[t] > 0 && alpha[t] < C) || (y[t] < 0 && alpha[t] > 0);
+      const int low = (y[t] > 0 && alpha[t] > 0) || (y[t] < 0 && alpha[t] < C);
+      if (up && v > m) { m = v; i = t; }
+      if (low && v < M) { M = v; j = t; }
+    }
+    if (i < 0 || j < 0 || m - M < tol) break;
+    const double yi = y[i], yj = y[j];
+    double eta = KK(i, i) + KK(j, j) - 2.0 * KK(i, j);
+    if (eta <= 1e-12) eta = 1e-12;
+    /* move along d = (y_i, -y_j) scaled: a_i += y_i s, a_j -= y_j s */
+    double s = (m - M) / eta;
+    /* box limits for s */
+    const double si = (yi > 0) ? C - alpha[i] : alpha[i];
+    const double sj = (yj > 0) ? alpha[j] : C - alpha[j];
+    if (s > si) s = si;
+    if (s > sj) s = sj;
+    alpha[i] += yi * s;
+    alpha[j] -= yj * s;
+    for (long long t = 0; t < n; ++t) g[t] += y[t] * s * (KK(t, i) - KK(t, j));
+  }
+  /* bias: average of -y_t g_t over free vectors, else midpoint of the bounds */
+  double sum = 0.0;
+  long long nf = 0;
+  for (long long t = 0; t < n; ++t)
+    if (alpha[t] > 0 && alpha[t] < C) {
+      sum += -y[t] * g[t];
+      ++nf;
+    }
+  *b_out = nf ? sum / (double)nf : 0.5 * (m + M);
+#undef KK
+  free(g);
+  return it;
+}
+
+/* f[r] = sum_i alpha_i y_i Kx[r][idx_i] + b for m rows of a cross kernel. */
+void qo_svc_decision(const double* Kx, long long ldk, const long long* idx, long long m, const double* alpha,
+                     const signed char* y, double b, long long n, double* f) {
+  for (long long r = 0; r < m; ++r) {
+    double acc = b;
+    for (long long i = 0; i < n; ++i) acc += alpha[i] * y[i] * Kx[r * ldk + (idx ? idx[i] : i)];
+    f[r] = acc;
+  }
+}

@@ -23,6 +23,17 @@ int num_pipe_shapes();
 cudaError_t launch_wait_timeout_selftest(uint64_t limit_ns, cudaStream_t st);
 cudaError_t launch_sv_gram(const double* X, int64_t N, int n, int reps, void* ws, double* K, int64_t ldk,
                            cudaStream_t st);
+struct DevSvcProblem {
+  const int64_t* idx;
+  const int8_t* y;
+  int64_t n;
+  double* alpha;
+  double* g;
+};
+cudaError_t launch_svc_fit(const double* K, int64_t ldk, const DevSvcProblem* probs, int n_probs, double C, double tol,
+                           int64_t max_iter, double* b_out, int64_t* iters_out, cudaStream_t st);
+cudaError_t launch_svc_decision(const double* Kx, int64_t ldk, int64_t m, const DevSvcProblem* probs, int n_probs,
+                                const double* b, double* F, cudaStream_t st);
 PipeCfg make_pipe(int chi, int prec, int shape);
 int pipe_smem(const PipeCfg& pc, int chi, int prec);
 }  // namespace qsvm
@@ -487,6 +498,79 @@ int32_t qsvm_sv_gram(const double* X, int64_t n_points, int32_t n_qubits, int32_
   if (ws_bytes < need) return fail(QSVM_ERR_WORKSPACE, "ws_bytes=%zu < required %zu", ws_bytes, need);
   cudaError_t e = launch_sv_gram(X, n_points, n_qubits, reps, ws, K, ldk, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "state-vector launch");
+  return QSVM_OK;
+}
+
+// ---- SVC on a precomputed kernel ----------------------------------------------
+static size_t svc_table_bytes(int32_t n_problems) {
+  return ((size_t)n_problems * sizeof(DevSvcProblem) + 255) / 256 * 256;
+}
+
+static int32_t svc_check(const qsvm_svc_problem* probs, int32_t n_problems) {
+  if (!probs || n_problems < 1 || n_problems > 65535)
+    return fail(QSVM_ERR_ARG, "problems must be a host array of 1..65535 entries");
+  for (int32_t p = 0; p < n_problems; ++p) {
+    const qsvm_svc_problem& P = probs[p];
+    if (!P.idx || !aligned(P.idx, 8) || !P.y || !P.alpha || !aligned(P.alpha, 8) || P.n < 2)
+      return fail(QSVM_ERR_ARG, "problem %d: null or misaligned pointer, or fewer than 2 points", p);
+  }
+  return QSVM_OK;
+}
+
+size_t qsvm_svc_workspace_bytes(const qsvm_svc_problem* problems, int32_t n_problems) {
+  if (!problems || n_problems < 1) return 0;
+  size_t g = 0;
+  for (int32_t p = 0; p < n_problems; ++p) g += (size_t)(problems[p].n > 0 ? problems[p].n : 0);
+  return svc_table_bytes(n_problems) + g * sizeof(double);
+}
+
+// writes the device problem table (and gradient slices) into ws on the stream
+static int32_t svc_upload(const qsvm_svc_problem* probs, int32_t n_problems, void* ws, bool with_g, cudaStream_t st) {
+  std::vector<DevSvcProblem> t((size_t)n_problems);
+  double* g = reinterpret_cast<double*>(static_cast<uint8_t*>(ws) + svc_table_bytes(n_problems));
+  for (int32_t p = 0; p < n_problems; ++p) {
+    t[(size_t)p] = DevSvcProblem{probs[p].idx, probs[p].y, probs[p].n, probs[p].alpha, with_g ? g : nullptr};
+    g += probs[p].n;
+  }
+  cudaError_t e = cudaMemcpyAsync(ws, t.data(), t.size() * sizeof(DevSvcProblem), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "svc problem table upload");
+  return QSVM_OK;
+}
+
+int32_t qsvm_svc_fit(const double* K, int64_t ldk, const qsvm_svc_problem* problems, int32_t n_problems, double C,
+                     double tol, int64_t max_iter, double* b_out, int64_t* iters_out, void* ws, size_t ws_bytes,
+                     void* stream) {
+  int32_t rc = svc_check(problems, n_problems);
+  if (rc) return rc;
+  if (!K || !aligned(K, 8) || ldk < 1) return fail(QSVM_ERR_ARG, "K must be a non-null 8-byte aligned device pointer");
+  if (!(C > 0) || !(tol > 0) || max_iter < 1) return fail(QSVM_ERR_ARG, "C and tol must be > 0, max_iter >= 1");
+  if (!b_out || !iters_out || !aligned(b_out, 8) || !aligned(iters_out, 8))
+    return fail(QSVM_ERR_ARG, "b_out and iters_out must be 8-byte aligned device pointers");
+  if (!ws || !aligned(ws, 256)) return fail(QSVM_ERR_ARG, "ws must be a non-null 256-byte aligned device pointer");
+  if (ws_bytes < qsvm_svc_workspace_bytes(problems, n_problems))
+    return fail(QSVM_ERR_WORKSPACE, "ws_bytes=%zu < required %zu", ws_bytes, qsvm_svc_workspace_bytes(problems, n_problems));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = svc_upload(problems, n_problems, ws, true, st);
+  if (rc) return rc;
+  cudaError_t e = launch_svc_fit(K, ldk, static_cast<const DevSvcProblem*>(ws), n_problems, C, tol, max_iter, b_out,
+                                 iters_out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "svc fit launch");
+  return QSVM_OK;
+}
+
+int32_t qsvm_svc_decision(const double* Kx, int64_t ldk, int64_t m, const qsvm_svc_problem* problems,
+                          int32_t n_problems, const double* b, double* F, void* ws, size_t ws_bytes, void* stream) {
+  int32_t rc = svc_check(problems, n_problems);
+  if (rc) return rc;
+  if (m < 1 || !Kx || !aligned(Kx, 8) || !b || !F || !aligned(F, 8))
+    return fail(QSVM_ERR_ARG, "Kx, b and F must be non-null aligned device pointers and m >= 1");
+  if (!ws || !aligned(ws, 256) || ws_bytes < svc_table_bytes(n_problems))
+    return fail(QSVM_ERR_WORKSPACE, "ws must hold the %zu-byte problem table", svc_table_bytes(n_problems));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = svc_upload(problems, n_problems, ws, false, st);
+  if (rc) return rc;
+  cudaError_t e = launch_svc_decision(Kx, ldk, m, static_cast<const DevSvcProblem*>(ws), n_problems, b, F, st);
+  if (e != cudaSuccess) return cuda_fail(e, "svc decision launch");
   return QSVM_OK;
 }
 

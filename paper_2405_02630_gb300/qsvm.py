@@ -48,6 +48,11 @@ class QsvmJob(ctypes.Structure):
                 ("logK", ctypes.c_void_p), ("ldl", ctypes.c_int64)]
 
 
+class QsvmSvcProblem(ctypes.Structure):
+    """Mirror of struct qsvm_svc_problem (include/qsvm.h)."""
+    _fields_ = [("idx", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n", ctypes.c_int64), ("alpha", ctypes.c_void_p)]
+
+
 _SIGS = {
     "qsvm_mps_record_bytes": (_sz, [_i32, _i32]),
     "qsvm_mps_bytes": (_sz, [_i32, _i32, _i64, _i32]),
@@ -75,6 +80,10 @@ _SIGS = {
     "qsvm_device_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
     "qsvm_selftest_wait_timeout": (_i32, [_i64, _vp]),
     "qsvm_sv_workspace_bytes": (_sz, [_i64, _i32]),
+    "qsvm_svc_workspace_bytes": (_sz, [ctypes.POINTER(QsvmSvcProblem), _i32]),
+    "qsvm_svc_fit": (_i32, [_dp, _i64, ctypes.POINTER(QsvmSvcProblem), _i32, ctypes.c_double, ctypes.c_double, _i64,
+                            _dp, _vp, _vp, _sz, _vp]),
+    "qsvm_svc_decision": (_i32, [_dp, _i64, _i64, ctypes.POINTER(QsvmSvcProblem), _i32, _dp, _dp, _vp, _sz, _vp]),
     "qsvm_sv_gram": (_i32, [_dp, _i64, _i32, _i32, _dp, _i64, _vp, _sz, _vp]),
     "qsvm_last_error": (ctypes.c_char_p, []),
     "qsvm_version": (ctypes.c_char_p, []),
@@ -315,6 +324,44 @@ def qsvm_sv_gram(X, reps: int, K=None, ws=None, stream=None):
         ws = torch.empty(max(16, qsvm_sv_workspace_bytes(N, n)), dtype=torch.uint8, device=X.device)
     _check(lib().qsvm_sv_gram(_ptr(X), N, n, reps, _ptr(K), K.stride(0), _ptr(ws), ws.numel(), _stream(stream)))
     return K
+
+
+# ------------------------------------------------------------------- SVC ---
+def _svc_array(problems):
+    """problems: list of dicts with idx (int64 tensor), y (int8 tensor), alpha (float64 tensor)."""
+    arr = (QsvmSvcProblem * len(problems))()
+    for k, p in enumerate(problems):
+        arr[k] = QsvmSvcProblem(p["idx"].data_ptr(), p["y"].data_ptr(), p["idx"].numel(), p["alpha"].data_ptr())
+    return arr
+
+
+def qsvm_svc_workspace_bytes(problems) -> int:
+    arr = _svc_array(problems)
+    return int(lib().qsvm_svc_workspace_bytes(arr, len(problems)))
+
+
+def qsvm_svc_fit(K, problems, C: float = 1.0, tol: float = 1e-8, max_iter: int = 10_000_000, stream=None):
+    """SMO on each binary problem (one CTA each).  Returns (b, iters) device tensors."""
+    import torch
+    arr = _svc_array(problems)
+    ws = torch.empty(max(256, int(lib().qsvm_svc_workspace_bytes(arr, len(problems)))), dtype=torch.uint8,
+                     device=K.device)
+    b = torch.empty(len(problems), dtype=torch.float64, device=K.device)
+    it = torch.empty(len(problems), dtype=torch.int64, device=K.device)
+    _check(lib().qsvm_svc_fit(_ptr(K), K.stride(0), arr, len(problems), C, tol, max_iter, _ptr(b), _ptr(it), _ptr(ws),
+                              ws.numel(), _stream(stream)))
+    return b, it
+
+
+def qsvm_svc_decision(Kx, problems, b, stream=None):
+    """F[r, p] = sum_i alpha_i y_i Kx[r, idx_i] + b[p]."""
+    import torch
+    arr = _svc_array(problems)
+    ws = torch.empty(max(256, 256 * ((len(problems) * 40 + 255) // 256)), dtype=torch.uint8, device=Kx.device)
+    F = torch.empty((Kx.shape[0], len(problems)), dtype=torch.float64, device=Kx.device)
+    _check(lib().qsvm_svc_decision(_ptr(Kx), Kx.stride(0), Kx.shape[0], arr, len(problems), _ptr(b), _ptr(F),
+                                   _ptr(ws), ws.numel(), _stream(stream)))
+    return F
 
 
 def qsvm_selftest_wait_timeout(limit_ns: int, stream=None):
