@@ -19,6 +19,13 @@
 // last site: right bond 1), with rep 1 in the most significant bit.  The last
 // repetition's copied bit is the low bit of the right bond and equals the
 // physical index, which is what the block layout of the record relies on.
+//
+// The low bit c of the left bond (the left neighbour's last-repetition spin)
+// enters the site tensor only through the last repetition's ZZ phase
+// exp(-i theta z(c) z(sigma)), so the rows with c = 1 are the rows with c = 0
+// times exp(2 i theta z(sigma)).  The record therefore keeps the c = 0 blocks
+// a_0s and the phase r = exp(2 i theta_{k-1}) (1 at site 0, where only t = 0
+// exists); the contraction applies the c = 1 half through r.
 #include "qsvm_common.cuh"
 
 namespace qsvm {
@@ -37,22 +44,21 @@ __device__ __forceinline__ void store_forms(uint8_t* pa, uint8_t* pb, float re, 
 }
 
 template <int CHI, int PREC>
-__device__ __forceinline__ void store_entry(uint8_t* recA, uint8_t* recB, int b, int q, int p, cd v) {
+__device__ __forceinline__ void store_entry(uint8_t* recA, uint8_t* recB, int off, cd v) {
   using Rec = Record<CHI, PREC>;
-  constexpr int H = CHI / 2;
-  const int off = b * Rec::kBlockBytes + (q * H + p) * Rec::kEntryBytes;
   if constexpr (PREC == QSVM_FP64) {
     reinterpret_cast<double2*>(recA + off)[0] = make_double2(v.re, v.im);
   } else if constexpr (PREC == QSVM_FP32) {
     store_forms(recA + off, recB + off, __double2float_rn(v.re), __double2float_rn(v.im));
   } else {
     // hi: nearest multiple of 2^-kGridT (exact in double and in float since
-    // |v| <= 1); lo: the remainder rounded to float.
+    // |v| <= 1); lo: the remainder rounded to float.  Block entries keep their
+    // lo part kPartBytes after the hi part; the phase keeps it in the next entry.
     constexpr double s = (double)(1 << kGridT);
     const double hr = rint(v.re * s) / s, hi = rint(v.im * s) / s;
+    const int lo_off = off < Rec::kPhaseOff ? Rec::kPartBytes : Rec::kEntryBytes;
     store_forms(recA + off, recB + off, (float)hr, (float)hi);
-    store_forms(recA + off + Rec::kPartBytes, recB + off + Rec::kPartBytes, __double2float_rn(v.re - hr),
-                __double2float_rn(v.im - hi));
+    store_forms(recA + off + lo_off, recB + off + lo_off, __double2float_rn(v.re - hr), __double2float_rn(v.im - hi));
   }
 }
 
@@ -132,7 +138,10 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
   uint8_t* recA = mps + gid * Rec::kBytes;
   uint8_t* recB = recA + (Rec::kForms == 2 ? n_points * (int64_t)n * Rec::kBytes : 0);
   const bool last = (k == n - 1);
-  for (int t = 0; t < CHI; ++t) {
+  constexpr int H = CHI / 2;
+  // rows t = 2q (c = 0) of both blocks s
+  for (int q = 0; q < H; ++q) {
+    const int t = 2 * q;
     cd v[2][CHI];
     if (!has_left && t > 0) {
 #pragma unroll
@@ -142,16 +151,17 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
     } else {
       site_row<R, false>(t, has_left, rz0, zzp, zzm, v);
     }
-    const int c = t & 1, q = t >> 1;
 #pragma unroll
     for (int u = 0; u < CHI; ++u) {
       const int s = u & 1, p = u >> 1;
       cd val;
       if (last) val = (u < 2) ? v[u][0] : cd{0.0, 0.0};
       else val = v[s][u];
-      store_entry<CHI, PREC>(recA, recB, 2 * c + s, q, p, val);
+      store_entry<CHI, PREC>(recA, recB, s * Rec::kBlockBytes + (q * H + p) * Rec::kEntryBytes, val);
     }
   }
+  // r = exp(2 i theta) = (zzm)^2: the ratio of the c = 1 rows to the c = 0 rows for sigma = 0
+  store_entry<CHI, PREC>(recA, recB, Rec::kPhaseOff, cmul(zzm, zzm));
 }
 
 template <int R, int PREC>

@@ -27,7 +27,13 @@ PipeCfg make_pipe(int chi, int prec, int shape) {
   PipeCfg pc;
   pc.S = kShapes[shape].chunk_bytes >= rec ? kShapes[shape].chunk_bytes / rec : 1;
   pc.stages = kShapes[shape].stages;
-  pc.slot_bytes = pc.S * rec + 16;
+  // A warp's lanes read 16-byte entries of up to 16 points' slots at once.  A slot
+  // stride that is an odd number of 16-byte units puts 8 consecutive slots in the
+  // 8 different 16-byte bank groups of a 128-byte row, so those reads take the
+  // minimum number of wavefronts (an even stride, e.g. 7 FP32 sites = 1008 + 16
+  // bytes, sends all 16 lanes to one group).
+  pc.slot_bytes = pc.S * rec;
+  if ((pc.slot_bytes / 16) % 2 == 0) pc.slot_bytes += 16;
   pc.stage_bytes = 2 * tile_side(chi, prec) * pc.slot_bytes;
   return pc;
 }

@@ -7,14 +7,18 @@
 //     amp = trace(E_n)   (the last site's right bond carries sigma).
 // The feature map ends on a diagonal layer, so A^sigma[t][u] vanishes unless the
 // low bit of u equals sigma; E is then block diagonal in (t & 1, t' & 1) and the
-// update splits into four chi/2-sized products per site (block b = 2c + s):
-//     E'_s = sum_c a_cs^T E_c conj(b_cs)            (chi^3 complex MACs per site)
-// which is a quarter of the dense 4 chi^3.
+// update splits into chi/2-sized blocks a_cs[q][p] = A^s[2q+c][2p+s]:
+//     E'_s = sum_c a_cs^T E_c conj(b_cs).
+// The low bit c of the left bond enters the site tensor only through the last
+// repetition's ZZ phase, so a_1s = r_s a_0s with r_0 = exp(2 i theta_{k-1}) and
+// r_1 = conj(r_0) (the record stores a_0s and r).  Hence
+//     E'_s = a_0s^T (E_0 + rho_s E_1) conj(b_0s),   rho_s = r_s(i) conj(r_s(j)),
+// chi^3/2 + chi^2/2 + 1 complex MACs per site instead of chi^3.
 //
 // One CTA owns a TI x TI tile of pairs, one thread per pair, E in registers for
 // all n sites.  The tile's 2*TI points stream their site records through shared
 // memory in chunks of S sites: one thread issues one bulk (TMA) copy per point
-// and chunk, completion is tracked by an mbarrier per stage, two stages in flight.
+// and chunk, completion is tracked by an mbarrier per stage.
 //
 // Renormalisation: E is scaled by an exact power of two 2^-e (max |component| of
 // E into [0.5, 1)) and e is accumulated in an integer, so the scale is exact.
@@ -67,58 +71,58 @@ struct Engine<CHI, QSVM_FP64> {
   }
 
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
-    double2 N[2][H][H];
+    // rho_0 = r(i) conj(r(j)); rho_1 = conj(rho_0)
+    const double2 ri = *reinterpret_cast<const double2*>(sptr(ra + Rec::kPhaseOff));
+    const double2 rj = *reinterpret_cast<const double2*>(sptr(rb + Rec::kPhaseOff));
+    const double pr = fma(ri.x, rj.x, ri.y * rj.y), pi = fma(ri.y, rj.x, -ri.x * rj.y);
+    // G_s = E_0 + rho_s E_1, in place: with T = E_0 + Re(rho) E_1,
+    // G_0 = T + Im(rho) i E_1 and G_1 = T - Im(rho) i E_1
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
+    for (int q = 0; q < H; ++q)
 #pragma unroll
-      for (int p = 0; p < H; ++p)
-#pragma unroll
-        for (int r = 0; r < H; ++r) N[s][p][r] = make_double2(0.0, 0.0);
+      for (int r = 0; r < H; ++r) {
+        const double2 e0 = E[0][q][r], e1 = E[1][q][r];
+        const double tr = fma(pr, e1.x, e0.x), ti = fma(pr, e1.y, e0.y);
+        E[0][q][r] = make_double2(fma(-pi, e1.y, tr), fma(pi, e1.x, ti));
+        E[1][q][r] = make_double2(fma(pi, e1.y, tr), fma(-pi, e1.x, ti));
+      }
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        double2 a[H][H], b[H][H];
-        load_block_d<H>(ra + (2 * c + s) * Rec::kBlockBytes, a);
-        load_block_d<H>(rb + (2 * c + s) * Rec::kBlockBytes, b);
-#pragma unroll
-        for (int p = 0; p < H; ++p) {
-          double2 X[H];
-#pragma unroll
-          for (int r = 0; r < H; ++r) {  // X[r] = sum_q a[q][p] E_c[q][r]
-            double xr = 0.0, xi = 0.0;
-#pragma unroll
-            for (int q = 0; q < H; ++q) {
-              const double2 A = a[q][p], e = E[c][q][r];
-              xr = fma(A.x, e.x, xr);
-              xr = fma(-A.y, e.y, xr);
-              xi = fma(A.x, e.y, xi);
-              xi = fma(A.y, e.x, xi);
-            }
-            X[r] = make_double2(xr, xi);
-          }
-#pragma unroll
-          for (int pp = 0; pp < H; ++pp) {  // N_s[p][pp] += sum_r X[r] conj(b[r][pp])
-            double nr = N[s][p][pp].x, ni = N[s][p][pp].y;
-#pragma unroll
-            for (int r = 0; r < H; ++r) {
-              const double2 B = b[r][pp];
-              nr = fma(X[r].x, B.x, nr);
-              nr = fma(X[r].y, B.y, nr);
-              ni = fma(X[r].y, B.x, ni);
-              ni = fma(-X[r].x, B.y, ni);
-            }
-            N[s][p][pp] = make_double2(nr, ni);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
+      double2 a[H][H], b[H][H];
+      load_block_d<H>(ra + s * Rec::kBlockBytes, a);
+      load_block_d<H>(rb + s * Rec::kBlockBytes, b);
+      double2 X[H][H];
 #pragma unroll
       for (int p = 0; p < H; ++p)
 #pragma unroll
-        for (int r = 0; r < H; ++r) E[s][p][r] = N[s][p][r];
+        for (int r = 0; r < H; ++r) {  // X[p][r] = sum_q a[q][p] G_s[q][r]
+          double xr = 0.0, xi = 0.0;
+#pragma unroll
+          for (int q = 0; q < H; ++q) {
+            const double2 A = a[q][p], g = E[s][q][r];
+            xr = fma(A.x, g.x, xr);
+            xr = fma(-A.y, g.y, xr);
+            xi = fma(A.x, g.y, xi);
+            xi = fma(A.y, g.x, xi);
+          }
+          X[p][r] = make_double2(xr, xi);
+        }
+#pragma unroll
+      for (int p = 0; p < H; ++p)
+#pragma unroll
+        for (int pp = 0; pp < H; ++pp) {  // E'_s[p][pp] = sum_r X[p][r] conj(b[r][pp])
+          double nr = 0.0, ni = 0.0;
+#pragma unroll
+          for (int r = 0; r < H; ++r) {
+            const double2 B = b[r][pp];
+            nr = fma(X[p][r].x, B.x, nr);
+            nr = fma(X[p][r].y, B.y, nr);
+            ni = fma(X[p][r].y, B.x, ni);
+            ni = fma(-X[p][r].x, B.y, ni);
+          }
+          E[s][p][pp] = make_double2(nr, ni);
+        }
+    }
   }
 
   __device__ __forceinline__ void renorm() {
@@ -165,6 +169,23 @@ __device__ __forceinline__ float2 grid_round2(float2 v) {
   return add2(add2(v, make_float2(C, C)), make_float2(-C, -C));
 }
 
+// The frexp exponent of a positive float: m in [2^(e-1), 2^e) for normal m; -126
+// for subnormal m (whose callers rescale in an extra exact step).
+__device__ __forceinline__ int exp_of(float m) { return (int)((__float_as_uint(m) >> 23) & 0xffu) - 126; }
+
+// Largest |component| of n packed values, as a tree (n a power of two).
+template <int NV>
+__device__ __forceinline__ float max_abs(const float2 (&v)[NV]) {
+  float t[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) t[i] = fmaxf(fabsf(v[i].x), fabsf(v[i].y));
+#pragma unroll
+  for (int w = NV / 2; w >= 1; w >>= 1)
+#pragma unroll
+    for (int i = 0; i < w; ++i) t[i] = fmaxf(t[i], t[i + w]);
+  return t[0];
+}
+
 // A block of form entries: first pair (A or conj B), second pair (iA or i conj B).
 template <int H>
 __device__ __forceinline__ void load_forms(uint32_t a, float2 (&x)[H][H], float2 (&ix)[H][H]) {
@@ -201,65 +222,59 @@ struct Engine<CHI, QSVM_FP32> {
   }
 
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
-    float2 N[2][H][H];
+    // rho_0 = r(i) conj(r(j)) from r(i)'s a-form components and r(j)'s b-form pair
+    const float4 fi = *reinterpret_cast<const float4*>(sptr(ra + Rec::kPhaseOff));
+    const float4 fj = *reinterpret_cast<const float4*>(sptr(rb + Rec::kPhaseOff));
+    const float2 rho = fma2(bc(fi.x), make_float2(fj.x, fj.y), mul2(bc(fi.y), make_float2(fj.z, fj.w)));
+    // forms: rho_0 = (a, b), i rho_0 = (-b, a); rho_1 = (a, -b), i rho_1 = (b, a)
+    const float2 R0 = rho, iR0 = make_float2(-rho.y, rho.x);
+    const float2 R1 = make_float2(rho.x, -rho.y), iR1 = make_float2(rho.y, rho.x);
+    // G_s = E_0 + rho_s E_1 = E_0 + E_1.re (rho_s) + E_1.im (i rho_s), in place
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
+    for (int q = 0; q < H; ++q)
 #pragma unroll
-      for (int p = 0; p < H; ++p)
-#pragma unroll
-        for (int r = 0; r < H; ++r) N[s][p][r] = make_float2(0.f, 0.f);
+      for (int r = 0; r < H; ++r) {
+        const float2 e0 = E[0][q][r], e1 = E[1][q][r];
+        E[0][q][r] = fma2(bc(e1.y), iR0, fma2(bc(e1.x), R0, e0));
+        E[1][q][r] = fma2(bc(e1.y), iR1, fma2(bc(e1.x), R1, e0));
+      }
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        float2 A[H][H], iA[H][H], cB[H][H], icB[H][H];
-        load_forms<H>(ra + (2 * c + s) * Rec::kBlockBytes, A, iA);
-        load_forms<H>(rb + (2 * c + s) * Rec::kBlockBytes, cB, icB);
-#pragma unroll
-        for (int p = 0; p < H; ++p) {
-          float2 X[H];
-#pragma unroll
-          for (int r = 0; r < H; ++r) {  // X[r] = sum_q a[q][p] E_c[q][r]
-            float2 x = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int q = 0; q < H; ++q) {
-              x = fma2(bc(E[c][q][r].x), A[q][p], x);
-              x = fma2(bc(E[c][q][r].y), iA[q][p], x);
-            }
-            X[r] = x;
-          }
-#pragma unroll
-          for (int pp = 0; pp < H; ++pp) {  // N_s[p][pp] += sum_r X[r] conj(b[r][pp])
-            float2 acc = N[s][p][pp];
-#pragma unroll
-            for (int r = 0; r < H; ++r) {
-              acc = fma2(bc(X[r].x), cB[r][pp], acc);
-              acc = fma2(bc(X[r].y), icB[r][pp], acc);
-            }
-            N[s][p][pp] = acc;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
+      float2 A[H][H], iA[H][H], cB[H][H], icB[H][H];
+      load_forms<H>(ra + s * Rec::kBlockBytes, A, iA);
+      load_forms<H>(rb + s * Rec::kBlockBytes, cB, icB);
+      float2 X[H][H];
 #pragma unroll
       for (int p = 0; p < H; ++p)
 #pragma unroll
-        for (int r = 0; r < H; ++r) E[s][p][r] = N[s][p][r];
+        for (int r = 0; r < H; ++r) {  // X[p][r] = sum_q a[q][p] G_s[q][r]
+          float2 x = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < H; ++q) {
+            x = fma2(bc(E[s][q][r].x), A[q][p], x);
+            x = fma2(bc(E[s][q][r].y), iA[q][p], x);
+          }
+          X[p][r] = x;
+        }
+#pragma unroll
+      for (int p = 0; p < H; ++p)
+#pragma unroll
+        for (int pp = 0; pp < H; ++pp) {  // E'_s[p][pp] = sum_r X[p][r] conj(b[r][pp])
+          float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int r = 0; r < H; ++r) {
+            acc = fma2(bc(X[p][r].x), cB[r][pp], acc);
+            acc = fma2(bc(X[p][r].y), icB[r][pp], acc);
+          }
+          E[s][p][pp] = acc;
+        }
+    }
   }
 
   __device__ __forceinline__ void renorm() {
-    float m = 0.f;
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int p = 0; p < H; ++p)
-#pragma unroll
-        for (int r = 0; r < H; ++r) m = fmaxf(m, fmaxf(fabsf(E[s][p][r].x), fabsf(E[s][p][r].y)));
+    const float m = max_abs<2 * H * H>(reinterpret_cast<const float2(&)[2 * H * H]>(E));
     if (!(m > 0.f) || !isfinite(m)) return;
-    int e;
-    frexpf(m, &e);
+    int e = exp_of(m);
     if (e < -120) {  // subnormal territory: scale in two exact steps
 #pragma unroll
       for (int s = 0; s < 2; ++s)
@@ -288,20 +303,59 @@ struct Engine<CHI, QSVM_FP32> {
 
 // Split FP32.  Every value v is carried as hi + lo: hi on a fixed binary grid,
 // lo the FP32 remainder.  Products of hi parts and their short sums are exact
-// in FP32 FMAs because they stay on a common grid below 2^24 units:
-//   step 1  X = a^T E_c:   hi(a) on 2^-11 with |hi(a)| <= 2^{-reps/2} + 2^-12,
-//           hi(E) on 2^-10 with |hi(E)| <= 1 + 2^-11 (E renormalised every site),
-//           2*(chi/2) real products per sum  ->  < 6.0e6 units of 2^-21 (chi <= 8);
-//   step 2  E' = sum_c X conj(b):  hi(X) on 2^-GX (GX = 9, or 8 for chi = 8) with
-//           |X| <= chi * 2^{-reps/2} (<= 2.83), hi(b) on 2^-11, 4*(chi/2) real
-//           products  ->  < 8.4e6 units of 2^-(GX+11)  (2^24 = 1.68e7).
-// The remaining terms use a = hi(a) + lo(a):
-//   a E = hi(a) hi(E) + hi(a) lo(E) + lo(a) full(E)      (step 1)
-//   X b = hi(X) hi(b) + full(X) lo(b) + lo(X) hi(b)      (step 2)
+// in FP32 FMAs because they stay on a common grid below 2^24 units (R = reps,
+// H = chi/2; |a|, |b| = 2^{-R/2}, |r| = 1; E renormalised to components <= 1):
+//   rho = r(i) conj(r(j)):  hi(r) on 2^-11, two products  ->  <= 2^23 units of 2^-22;
+//   G = E_0 + rho E_1:      hi(E) on 2^-10, hi(rho) on 2^-11, three terms
+//                           ->  < 3 * 2^21 units of 2^-21;  |G| <= 1 + sqrt(2);
+//   X = a^T G:              hi(G) on 2^-10, hi(a) on 2^-11, 2H products
+//                           ->  <= 1.44e7 units of 2^-21 (chi = 8; 1.0e7 for chi = 4);
+//   E' = X conj(b):         |X| <= H 2^{-R/2} 2 sqrt(2), hi(X) on 2^-GX (GX = 10, or
+//                           9 for chi = 8), 2H products  ->  < 1.19e7 units of 2^-(GX+11)
+//   (2^24 = 1.68e7).
+// The remaining terms use u = hi(u) + lo(u):
+//   u w = hi(u) hi(w) + hi(u) lo(w) + lo(u) full(w)
 // where full() is the rounded FP32 sum hi + lo.  Each correction is about 2^-11
-// of the result, so its FP32 rounding costs ~2^-35 relative per site; nothing
+// of the result, so its FP32 rounding costs ~2^-35 relative per step; nothing
 // else is rounded.  This is the split hi+lo compensated product carried out on
 // the FP32 pipe: 6 packed FMAs (12 FMAs) per complex MAC.
+
+// rho_s = r_s(i) conj(r_s(j)) as split forms: R[s] = rho_s, iR[s] = i rho_s (hi and lo).
+__device__ __forceinline__ void split_phase(uint32_t pa, uint32_t pb, float2 (&Rh)[2], float2 (&iRh)[2],
+                                            float2 (&Rl)[2], float2 (&iRl)[2]) {
+  const float4 ih = *reinterpret_cast<const float4*>(sptr(pa));
+  const float4 il = *reinterpret_cast<const float4*>(sptr(pa + 16));
+  const float4 jh = *reinterpret_cast<const float4*>(sptr(pb));
+  const float4 jl = *reinterpret_cast<const float4*>(sptr(pb + 16));
+  const float2 cjh = make_float2(jh.x, jh.y), icjh = make_float2(jh.z, jh.w);
+  const float2 cjl = make_float2(jl.x, jl.y), icjl = make_float2(jl.z, jl.w);
+  const float2 h = fma2(bc(ih.x), cjh, mul2(bc(ih.y), icjh));  // exact
+  const float fx = ih.x + il.x, fy = ih.y + il.y;
+  const float2 l = fma2(bc(il.x), cjh, fma2(bc(il.y), icjh, fma2(bc(fx), cjl, mul2(bc(fy), icjl))));
+  const float2 v = add2(h, l);
+  const float2 rh = grid_round2<kGridT>(v);
+  const float2 rl = add2(fma2(rh, make_float2(-1.f, -1.f), h), l);  // (h - rh) is exact
+  Rh[0] = rh;
+  iRh[0] = make_float2(-rh.y, rh.x);
+  Rh[1] = make_float2(rh.x, -rh.y);
+  iRh[1] = make_float2(rh.y, rh.x);
+  Rl[0] = rl;
+  iRl[0] = make_float2(-rl.y, rl.x);
+  Rl[1] = make_float2(rl.x, -rl.y);
+  iRl[1] = make_float2(rl.y, rl.x);
+}
+
+// G = E_0 + rho E_1 split onto the 2^-kGridG grid (hi, lo, full).
+__device__ __forceinline__ void split_mix(float2 e0h, float2 e0l, float2 e1h, float2 e1l, float2 e1f, float2 Rh,
+                                          float2 iRh, float2 Rl, float2 iRl, float2& gh, float2& gl, float2& gf) {
+  const float2 h = fma2(bc(e1h.y), iRh, fma2(bc(e1h.x), Rh, e0h));  // exact
+  const float2 l = fma2(bc(e1f.y), iRl, fma2(bc(e1f.x), Rl, fma2(bc(e1l.y), iRh, fma2(bc(e1l.x), Rh, e0l))));
+  const float2 v = add2(h, l);
+  gh = grid_round2<kGridG>(v);
+  gl = add2(fma2(gh, make_float2(-1.f, -1.f), h), l);  // (h - gh) is exact
+  gf = v;
+}
+
 template <int CHI>
 struct Engine<CHI, QSVM_FP32_SPLIT> {
   static constexpr int H = CHI / 2;
@@ -324,86 +378,87 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
 
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     const float2 m1 = make_float2(-1.f, -1.f);
+    float2 Rh[2], iRh[2], Rl[2], iRl[2];
+    split_phase(ra + Rec::kPhaseOff, rb + Rec::kPhaseOff, Rh, iRh, Rl, iRl);
+    // G_s = E_0 + rho_s E_1, in place of E_s
+#pragma unroll
+    for (int q = 0; q < H; ++q)
+#pragma unroll
+      for (int r = 0; r < H; ++r) {
+        const float2 e0h = Eh[0][q][r], e0l = El[0][q][r];
+        const float2 e1h = Eh[1][q][r], e1l = El[1][q][r], e1f = Ef[1][q][r];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          split_mix(e0h, e0l, e1h, e1l, e1f, Rh[s], iRh[s], Rl[s], iRl[s], Eh[s][q][r], El[s][q][r], Ef[s][q][r]);
+      }
     float2 Nh[2][H][H], Nl[2][H][H];
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int p = 0; p < H; ++p)
-#pragma unroll
-        for (int r = 0; r < H; ++r) Nh[s][p][r] = Nl[s][p][r] = make_float2(0.f, 0.f);
-#pragma unroll
     for (int s = 0; s < 2; ++s) {
+      const uint32_t pa = ra + s * Rec::kBlockBytes;
+      const uint32_t pb = rb + s * Rec::kBlockBytes;
+      float2 Ah[H][H], iAh[H][H], Al[H][H], iAl[H][H];
+      float2 Bh[H][H], iBh[H][H], Bl[H][H], iBl[H][H];  // conj(b) and i conj(b), hi and lo
+      load_forms<H>(pa, Ah, iAh);
+      load_forms<H>(pa + Rec::kPartBytes, Al, iAl);
+      load_forms<H>(pb, Bh, iBh);
+      load_forms<H>(pb + Rec::kPartBytes, Bl, iBl);
+      // X[p][r] = sum_q a[q][p] G_s[q][r]
+      float2 Xh[H][H], Xl[H][H], Xf[H][H];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const uint32_t pa = ra + (2 * c + s) * Rec::kBlockBytes;
-        const uint32_t pb = rb + (2 * c + s) * Rec::kBlockBytes;
-        float2 Ah[H][H], iAh[H][H], Al[H][H], iAl[H][H];
-        float2 Bh[H][H], iBh[H][H], Bl[H][H], iBl[H][H];  // conj(b) and i conj(b), hi and lo
-        load_forms<H>(pa, Ah, iAh);
-        load_forms<H>(pa + Rec::kPartBytes, Al, iAl);
-        load_forms<H>(pb, Bh, iBh);
-        load_forms<H>(pb + Rec::kPartBytes, Bl, iBl);
-        // step 1: X[p][r] = sum_q a[q][p] E_c[q][r]
-        float2 Xh[H][H], Xl[H][H], Xf[H][H];
+      for (int p = 0; p < H; ++p) {
 #pragma unroll
-        for (int p = 0; p < H; ++p) {
+        for (int r = 0; r < H; ++r) {
+          float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < H; ++q) {
+            const float2 g = Eh[s][q][r], gl = El[s][q][r], gf = Ef[s][q][r];
+            h = fma2(bc(g.x), Ah[q][p], h);
+            h = fma2(bc(g.y), iAh[q][p], h);
+            l = fma2(bc(gl.x), Ah[q][p], l);
+            l = fma2(bc(gl.y), iAh[q][p], l);
+            l = fma2(bc(gf.x), Al[q][p], l);
+            l = fma2(bc(gf.y), iAl[q][p], l);
+          }
+          const float2 v = add2(h, l);
+          const float2 xh = grid_round2<GX>(v);
+          Xh[p][r] = xh;
+          Xl[p][r] = add2(fma2(xh, m1, h), l);  // (h - xh) is exact
+          Xf[p][r] = v;
+        }
+      }
+      // E'_s[p][pp] = sum_r X[p][r] conj(b[r][pp])
+#pragma unroll
+      for (int p = 0; p < H; ++p) {
+#pragma unroll
+        for (int pp = 0; pp < H; ++pp) {
+          float2 hh = make_float2(0.f, 0.f), ll = make_float2(0.f, 0.f);
 #pragma unroll
           for (int r = 0; r < H; ++r) {
-            float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int q = 0; q < H; ++q) {
-              const float2 e = Eh[c][q][r], el = El[c][q][r], ef = Ef[c][q][r];
-              h = fma2(bc(e.x), Ah[q][p], h);
-              h = fma2(bc(e.y), iAh[q][p], h);
-              l = fma2(bc(el.x), Ah[q][p], l);
-              l = fma2(bc(el.y), iAh[q][p], l);
-              l = fma2(bc(ef.x), Al[q][p], l);
-              l = fma2(bc(ef.y), iAl[q][p], l);
-            }
-            const float2 v = add2(h, l);
-            const float2 xh = grid_round2<GX>(v);
-            Xh[p][r] = xh;
-            Xl[p][r] = add2(fma2(xh, m1, h), l);  // (h - xh) is exact
-            Xf[p][r] = v;
+            const float2 xh = Xh[p][r], xl = Xl[p][r], xf = Xf[p][r];
+            hh = fma2(bc(xh.x), Bh[r][pp], hh);
+            hh = fma2(bc(xh.y), iBh[r][pp], hh);
+            ll = fma2(bc(xf.x), Bl[r][pp], ll);
+            ll = fma2(bc(xf.y), iBl[r][pp], ll);
+            ll = fma2(bc(xl.x), Bh[r][pp], ll);
+            ll = fma2(bc(xl.y), iBh[r][pp], ll);
           }
-        }
-        // step 2: N_s[p][pp] += sum_r X[p][r] conj(b[r][pp])
-#pragma unroll
-        for (int p = 0; p < H; ++p) {
-#pragma unroll
-          for (int pp = 0; pp < H; ++pp) {
-            float2 hh = Nh[s][p][pp], ll = Nl[s][p][pp];
-#pragma unroll
-            for (int r = 0; r < H; ++r) {
-              const float2 xh = Xh[p][r], xl = Xl[p][r], xf = Xf[p][r];
-              hh = fma2(bc(xh.x), Bh[r][pp], hh);
-              hh = fma2(bc(xh.y), iBh[r][pp], hh);
-              ll = fma2(bc(xf.x), Bl[r][pp], ll);
-              ll = fma2(bc(xf.y), iBl[r][pp], ll);
-              ll = fma2(bc(xl.x), Bh[r][pp], ll);
-              ll = fma2(bc(xl.y), iBh[r][pp], ll);
-            }
-            Nh[s][p][pp] = hh;
-            Nl[s][p][pp] = ll;
-          }
+          Nh[s][p][pp] = hh;
+          Nl[s][p][pp] = ll;
         }
       }
     }
     // renormalise by 2^-e (max |component| of hi + lo into [0.5, 1)) and re-split onto the E grid
     float2 V[2][H][H];
-    float m = 0.f;
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
       for (int p = 0; p < H; ++p)
 #pragma unroll
-        for (int r = 0; r < H; ++r) {
-          V[s][p][r] = add2(Nh[s][p][r], Nl[s][p][r]);
-          m = fmaxf(m, fmaxf(fabsf(V[s][p][r].x), fabsf(V[s][p][r].y)));
-        }
+        for (int r = 0; r < H; ++r) V[s][p][r] = add2(Nh[s][p][r], Nl[s][p][r]);
+    const float m = max_abs<2 * H * H>(reinterpret_cast<const float2(&)[2 * H * H]>(V));
     int e = 0;
     if (m > 0.f && isfinite(m)) {
-      frexpf(m, &e);
+      e = exp_of(m);
       if (e < -120) {  // collapse to near zero: scale up in two exact steps
         const float2 up = bc(pow2f(100));
 #pragma unroll
@@ -452,14 +507,14 @@ __device__ int32_t g_pair_status;
 
 // Split FP32 at chi = 8 with four threads per pair.  One thread cannot hold a
 // pair's split environment (2 blocks x 16 entries x hi/lo/full = 192 floats) in
-// registers, so thread (s, h) of a quad owns rows {2h, 2h+1} of block s of the
-// new environment.  Per site it reads the whole old environment from a padded
-// shared buffer (every row is needed: X[p][r] = sum_q a[q][p] E_c[q][r]), builds
-// its two rows of X_cs for c = 0, 1, accumulates its two rows of
-// E'_s = sum_c X_cs conj(b_cs), and after a warp barrier writes them back.  The
-// quad agrees on the power-of-two rescale through two xor-shuffles.  The
-// arithmetic per entry is exactly that of Engine<8, QSVM_FP32_SPLIT>: the same
-// grids, the same three products per real MAC.
+// registers, so thread (s, h) of a quad owns rows {2h, 2h+1} of block s.  Per
+// site it mixes its rows of G_s = E_0 + rho_s E_1 from the same rows of E_0 and
+// E_1, publishes them in a padded shared buffer, reads all of G_s back (every
+// row is needed: X[p][r] = sum_q a[q][p] G_s[q][r]), builds its two rows of X,
+// accumulates its two rows of E'_s = X conj(b_0s) and writes them back; warp
+// barriers separate the reads and writes of the buffer.  The quad agrees on the
+// power-of-two rescale through two xor-shuffles.  Grids and products per entry
+// are those of Engine<8, QSVM_FP32_SPLIT>.
 template <int PREC>
 struct QuadEngine;
 
@@ -490,101 +545,121 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
     __syncwarp(mask);
   }
 
+  __device__ __forceinline__ float4* entry(int c, int q, int r) const {
+    return reinterpret_cast<float4*>(ebuf + (c * 16 + q * 4 + r) * 4);
+  }
+
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     const float2 m1 = make_float2(-1.f, -1.f);
-    float2 Nh[2][H], Nl[2][H];  // own rows p = 2h + {0, 1} of E'_s
+    float2 Rh[2], iRh[2], Rl[2], iRl[2];
+    split_phase(ra + Rec::kPhaseOff, rb + Rec::kPhaseOff, Rh, iRh, Rl, iRl);
+    const float2 rh = s ? Rh[1] : Rh[0], irh = s ? iRh[1] : iRh[0];
+    const float2 rl = s ? Rl[1] : Rl[0], irl = s ? iRl[1] : iRl[0];
+    // own rows of G_s from the same rows of E_0 and E_1
+    float4 Gq[2][H];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int r = 0; r < H; ++r) {
+        const float4 v0 = *entry(0, 2 * h + j, r), v1 = *entry(1, 2 * h + j, r);
+        const float2 e1h = make_float2(v1.x, v1.y), e1l = make_float2(v1.z, v1.w);
+        float2 gh, gl, gf;
+        split_mix(make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), e1h, e1l, add2(e1h, e1l), rh, irh, rl, irl, gh,
+                  gl, gf);
+        Gq[j][r] = make_float4(gh.x, gh.y, gl.x, gl.y);
+      }
+    __syncwarp(mask);  // every thread has read its rows of the old environment
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int r = 0; r < H; ++r) *entry(s, 2 * h + j, r) = Gq[j][r];
+    __syncwarp(mask);  // G_0 and G_1 are complete
+    const uint32_t pa = ra + s * Rec::kBlockBytes;
+    const uint32_t pb = rb + s * Rec::kBlockBytes;
+    // X[p][r] = sum_q a[q][p] G_s[q][r] for the thread's two rows p
+    float2 Xh[2][H], Xl[2][H], Xf[2][H];
+    {
+      float2 hh[2][H], ll[2][H];
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < H; ++r) hh[p][r] = ll[p][r] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < H; ++q) {
+        float2 Ah[2], iAh[2], Al[2], iAl[2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const float4 va = *reinterpret_cast<const float4*>(sptr(pa + (q * H + 2 * h + p) * 16));
+          const float4 vl = *reinterpret_cast<const float4*>(sptr(pa + Rec::kPartBytes + (q * H + 2 * h + p) * 16));
+          Ah[p] = make_float2(va.x, va.y);
+          iAh[p] = make_float2(va.z, va.w);
+          Al[p] = make_float2(vl.x, vl.y);
+          iAl[p] = make_float2(vl.z, vl.w);
+        }
+#pragma unroll
+        for (int r = 0; r < H; ++r) {
+          const float4 gv = *entry(s, q, r);
+          const float2 g = make_float2(gv.x, gv.y), gl = make_float2(gv.z, gv.w);
+          const float2 gf = add2(g, gl);
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            hh[p][r] = fma2(bc(g.x), Ah[p], hh[p][r]);
+            hh[p][r] = fma2(bc(g.y), iAh[p], hh[p][r]);
+            ll[p][r] = fma2(bc(gl.x), Ah[p], ll[p][r]);
+            ll[p][r] = fma2(bc(gl.y), iAh[p], ll[p][r]);
+            ll[p][r] = fma2(bc(gf.x), Al[p], ll[p][r]);
+            ll[p][r] = fma2(bc(gf.y), iAl[p], ll[p][r]);
+          }
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < H; ++r) {
+          const float2 v = add2(hh[p][r], ll[p][r]);
+          const float2 xh = grid_round2<GX>(v);
+          Xh[p][r] = xh;
+          Xl[p][r] = add2(fma2(xh, m1, hh[p][r]), ll[p][r]);
+          Xf[p][r] = v;
+        }
+    }
+    // E'_s[p][pp] = sum_r X[p][r] conj(b[r][pp])
+    float2 Nh[2][H], Nl[2][H];
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
       for (int pp = 0; pp < H; ++pp) Nh[p][pp] = Nl[p][pp] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const uint32_t pa = ra + (2 * c + s) * Rec::kBlockBytes;
-      const uint32_t pb = rb + (2 * c + s) * Rec::kBlockBytes;
-      // step 1: X[p][r] = sum_q a[q][p] E_c[q][r] for the thread's two rows p
-      float2 Xh[2][H], Xl[2][H], Xf[2][H];
-      {
-        float2 hh[2][H], ll[2][H];
+    for (int r = 0; r < H; ++r) {
 #pragma unroll
-        for (int p = 0; p < 2; ++p)
+      for (int pp = 0; pp < H; ++pp) {
+        const float4 vb = reinterpret_cast<const float4*>(sptr(pb + (r * H + pp) * 16))[0];
+        const float4 vl = reinterpret_cast<const float4*>(sptr(pb + Rec::kPartBytes + (r * H + pp) * 16))[0];
+        const float2 Bh = make_float2(vb.x, vb.y), iBh = make_float2(vb.z, vb.w);
+        const float2 Bl = make_float2(vl.x, vl.y), iBl = make_float2(vl.z, vl.w);
 #pragma unroll
-          for (int r = 0; r < H; ++r) hh[p][r] = ll[p][r] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < H; ++q) {
-          float2 Ah[2], iAh[2], Al[2], iAl[2];
-#pragma unroll
-          for (int p = 0; p < 2; ++p) {
-            const float4* fa = reinterpret_cast<const float4*>(sptr(pa + (q * H + 2 * h + p) * 16));
-            const float4* fl = reinterpret_cast<const float4*>(sptr(pa + Rec::kPartBytes + (q * H + 2 * h + p) * 16));
-            const float4 va = fa[0], vl = fl[0];
-            Ah[p] = make_float2(va.x, va.y);
-            iAh[p] = make_float2(va.z, va.w);
-            Al[p] = make_float2(vl.x, vl.y);
-            iAl[p] = make_float2(vl.z, vl.w);
-          }
-#pragma unroll
-          for (int r = 0; r < H; ++r) {
-            const float4 ev = *reinterpret_cast<const float4*>(ebuf + (c * 16 + q * 4 + r) * 4);
-            const float2 e = make_float2(ev.x, ev.y), el = make_float2(ev.z, ev.w);
-            const float2 ef = add2(e, el);
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-              hh[p][r] = fma2(bc(e.x), Ah[p], hh[p][r]);
-              hh[p][r] = fma2(bc(e.y), iAh[p], hh[p][r]);
-              ll[p][r] = fma2(bc(el.x), Ah[p], ll[p][r]);
-              ll[p][r] = fma2(bc(el.y), iAh[p], ll[p][r]);
-              ll[p][r] = fma2(bc(ef.x), Al[p], ll[p][r]);
-              ll[p][r] = fma2(bc(ef.y), iAl[p], ll[p][r]);
-            }
-          }
-        }
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-          for (int r = 0; r < H; ++r) {
-            const float2 v = add2(hh[p][r], ll[p][r]);
-            const float2 xh = grid_round2<GX>(v);
-            Xh[p][r] = xh;
-            Xl[p][r] = add2(fma2(xh, m1, hh[p][r]), ll[p][r]);
-            Xf[p][r] = v;
-          }
-      }
-      // step 2: N[p][pp] += sum_r X[p][r] conj(b[r][pp])
-#pragma unroll
-      for (int r = 0; r < H; ++r) {
-#pragma unroll
-        for (int pp = 0; pp < H; ++pp) {
-          const float4 vb = reinterpret_cast<const float4*>(sptr(pb + (r * H + pp) * 16))[0];
-          const float4 vl = reinterpret_cast<const float4*>(sptr(pb + Rec::kPartBytes + (r * H + pp) * 16))[0];
-          const float2 Bh = make_float2(vb.x, vb.y), iBh = make_float2(vb.z, vb.w);
-          const float2 Bl = make_float2(vl.x, vl.y), iBl = make_float2(vl.z, vl.w);
-#pragma unroll
-          for (int p = 0; p < 2; ++p) {
-            Nh[p][pp] = fma2(bc(Xh[p][r].x), Bh, Nh[p][pp]);
-            Nh[p][pp] = fma2(bc(Xh[p][r].y), iBh, Nh[p][pp]);
-            Nl[p][pp] = fma2(bc(Xf[p][r].x), Bl, Nl[p][pp]);
-            Nl[p][pp] = fma2(bc(Xf[p][r].y), iBl, Nl[p][pp]);
-            Nl[p][pp] = fma2(bc(Xl[p][r].x), Bh, Nl[p][pp]);
-            Nl[p][pp] = fma2(bc(Xl[p][r].y), iBh, Nl[p][pp]);
-          }
+        for (int p = 0; p < 2; ++p) {
+          Nh[p][pp] = fma2(bc(Xh[p][r].x), Bh, Nh[p][pp]);
+          Nh[p][pp] = fma2(bc(Xh[p][r].y), iBh, Nh[p][pp]);
+          Nl[p][pp] = fma2(bc(Xf[p][r].x), Bl, Nl[p][pp]);
+          Nl[p][pp] = fma2(bc(Xf[p][r].y), iBl, Nl[p][pp]);
+          Nl[p][pp] = fma2(bc(Xl[p][r].x), Bh, Nl[p][pp]);
+          Nl[p][pp] = fma2(bc(Xl[p][r].y), iBh, Nl[p][pp]);
         }
       }
     }
     // quad-wide rescale by 2^-e, then split onto the E grid
     float2 V[2][H];
-    float m = 0.f;
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
-      for (int pp = 0; pp < H; ++pp) {
-        V[p][pp] = add2(Nh[p][pp], Nl[p][pp]);
-        m = fmaxf(m, fmaxf(fabsf(V[p][pp].x), fabsf(V[p][pp].y)));
-      }
+      for (int pp = 0; pp < H; ++pp) V[p][pp] = add2(Nh[p][pp], Nl[p][pp]);
+    float m = max_abs<2 * H>(reinterpret_cast<const float2(&)[2 * H]>(V));
     m = fmaxf(m, __shfl_xor_sync(mask, m, 1));
     m = fmaxf(m, __shfl_xor_sync(mask, m, 2));
     int e = 0;
     if (m > 0.f && isfinite(m)) {
-      frexpf(m, &e);
+      e = exp_of(m);
       if (e < -120) {
         const float2 up = bc(pow2f(100));
 #pragma unroll
@@ -600,7 +675,7 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
       }
     }
     const float2 sc = bc(pow2f(-e));
-    __syncwarp(mask);  // every thread of the warp has read the old environment
+    __syncwarp(mask);  // every thread of the warp has read G
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
@@ -608,7 +683,7 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
         const float2 f = mul2(V[p][pp], sc);
         const float2 hv = grid_round2<kGridE>(f);
         const float2 lv = fma2(Nl[p][pp], sc, fma2(hv, m1, mul2(Nh[p][pp], sc)));
-        *reinterpret_cast<float4*>(ebuf + (s * 16 + (2 * h + p) * 4 + pp) * 4) = make_float4(hv.x, hv.y, lv.x, lv.y);
+        *entry(s, 2 * h + p, pp) = make_float4(hv.x, hv.y, lv.x, lv.y);
       }
     __syncwarp(mask);  // the new environment is complete before anyone reads it
     L += e;
@@ -618,8 +693,8 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
 
   // amplitude = E_0[0][0] + E_1[0][0] (both in the shared buffer after the last site)
   __device__ __forceinline__ void amplitude(double& re, double& im) const {
-    const float4 a = *reinterpret_cast<const float4*>(ebuf + (0 * 16 + 0) * 4);
-    const float4 b = *reinterpret_cast<const float4*>(ebuf + (1 * 16 + 0) * 4);
+    const float4 a = *entry(0, 0, 0);
+    const float4 b = *entry(1, 0, 0);
     re = ((double)a.x + (double)a.z) + ((double)b.x + (double)b.z);
     im = ((double)a.y + (double)a.w) + ((double)b.y + (double)b.w);
   }
@@ -645,7 +720,7 @@ __host__ __device__ constexpr int ebuf_bytes(int chi, int prec) {
 
 template <int CHI, int PREC>
 __host__ __device__ constexpr int min_blocks_per_sm() {
-  return (threads_per_pair(CHI, PREC) == 4) ? 2 : (CHI >= 8) ? 1 : ((PREC == QSVM_FP32) ? 3 : 2);
+  return (threads_per_pair(CHI, PREC) == 4) ? 2 : (CHI >= 8) ? 1 : ((PREC == QSVM_FP32_SPLIT) ? 2 : 3);
 }
 
 // Shared-memory control block at the end of the dynamic allocation.
@@ -719,22 +794,29 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
   const int nchunks = (n + S - 1) / S;
   const int g0 = gchunk;
 
+  // Issue chunk ch into its stage, by one whole warp: lane 0 posts the expected
+  // bytes on the stage's mbarrier, then lane l < ni copies row point l and lane
+  // ni + l < ni + nj column point l (ni + nj <= 2 TI <= 32).
   auto issue = [&](int ch) {
     const int g = g0 + ch;
     const int st = g % NST;
     const int k0 = ch * S;
     const int ns = min(S, n - k0);
     const uint32_t bytes = (uint32_t)(ns * Rec::kBytes);
-    mbar_arrive_expect_tx(&ctl->bars[st], bytes * (uint32_t)(ni + nj));
+    if (lane == 0) mbar_arrive_expect_tx(&ctl->bars[st], bytes * (uint32_t)(ni + nj));
+    __syncwarp();
     uint8_t* base = smem + st * STAGE;
-    for (int p = 0; p < ni; ++p)
-      bulk_g2s(base + p * SLOT, w.mpsA + ((i0 + p) * (int64_t)n + k0) * Rec::kBytes, bytes, &ctl->bars[st]);
-    for (int p = 0; p < nj; ++p)
+    if (lane < ni) {
+      bulk_g2s(base + lane * SLOT, w.mpsA + ((i0 + lane) * (int64_t)n + k0) * Rec::kBytes, bytes, &ctl->bars[st]);
+    } else if (lane < ni + nj) {
+      const int p = lane - ni;
       bulk_g2s(base + (TI + p) * SLOT, w.mpsB + ((j0 + p) * (int64_t)n + k0) * Rec::kBytes, bytes, &ctl->bars[st]);
-    ctl->issued = g + 1;
+    }
+    if (lane == 0) ctl->issued = g + 1;
   };
+  static_assert(2 * TI <= 32, "one lane per point of a tile");
 
-  if (tid == 0)
+  if (tid < 32)
     for (int ch = 0; ch < min(NST, nchunks); ++ch) issue(ch);
   __syncthreads();
 
@@ -757,11 +839,11 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
         if (*(volatile int*)&ctl->abort_flag || global_ns() - t0 > kWaitLimitNs) break;
       }
     }
+    ok = __all_sync(0xffffffffu, ok);  // the warp acts on one outcome
     if (!ok) {
-      *(volatile int*)&ctl->abort_flag = 1;
+      if (lane == 0) *(volatile int*)&ctl->abort_flag = 1;
       break;
     }
-    __syncwarp();
     const uint32_t base = smem_u32(smem) + st * STAGE;
     const int k0 = ch * S;
     const int ns = min(S, n - k0);
@@ -778,18 +860,18 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
       }
     }
     __syncwarp();
+    // all shared-memory reads of this warp for the stage are complete (their
+    // values were consumed above); count the warp out and, if last, refill
+    int last = 0;
     if (lane == 0) {
-      // all shared-memory reads of this warp for the stage are complete (their
-      // values were consumed above); count the warp out and, if last, refill
       __threadfence_block();
-      const int prev = atomicAdd(&ctl->done[st], 1);
-      if (prev == kTileWarps - 1) {
-        ctl->done[st] = 0;
-        if (ch + NST < nchunks) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          issue(ch + NST);
-        }
-      }
+      last = atomicAdd(&ctl->done[st], 1) == kTileWarps - 1;
+      if (last) ctl->done[st] = 0;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last && ch + NST < nchunks) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(ch + NST);
     }
   }
   __syncthreads();

@@ -1,7 +1,8 @@
 // qsvm_common.cuh -- device-side helpers shared by the libqsvm kernels.
 //
-// Site-record layout (see include/qsvm.h): four chi/2 x chi/2 blocks per site,
-// block b = 2c + s holds a_cs[q][p] = A[s][2q+c][2p+s]; entries complex.
+// Site-record layout (see include/qsvm.h): the two chi/2 x chi/2 blocks
+// a_0s[q][p] = A[s][2q][2p+s] (s = 0, 1), then the phase r = e^{2 i theta_k}
+// that gives the other two, a_1s = r_s a_0s with r_0 = r and r_1 = conj(r).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -14,38 +15,48 @@ namespace qsvm {
 
 constexpr double kPi = 3.14159265358979323846;
 
-// Binary grids of the split-FP32 format.  Tensor hi parts sit on 2^-kGridT;
-// environment hi parts on 2^-kGridE after renormalisation to max |.| < 1;
-// intermediate (A^T E) hi parts on 2^-kGridX(chi).  The exactness argument
-// (every hi*hi partial sum stays below 2^24 grid units) is spelled out in
-// pair_contract.cu.
+// Binary grids of the split-FP32 format.  Tensor and phase hi parts sit on
+// 2^-kGridT; environment hi parts on 2^-kGridE after renormalisation to
+// max |.| < 1; the mixed environment G = E_0 + rho E_1 on 2^-kGridG; the
+// intermediate (a^T G) on 2^-grid_x(chi).  The exactness argument (every hi*hi
+// partial sum stays below 2^24 grid units) is spelled out in pair_contract.cuh.
 constexpr int kGridT = 11;
 constexpr int kGridE = 10;
-__host__ __device__ constexpr int grid_x(int chi) { return chi >= 8 ? 8 : 9; }
+constexpr int kGridG = 10;
+__host__ __device__ constexpr int grid_x(int chi) { return chi >= 8 ? 9 : 10; }
 
-// Site-record geometry.  FP64 records hold each entry once as (re, im).  The
-// FP32 formats hold two forms of every record, in two arrays (all row-side
-// "a-form" records of the buffer first, then all column-side "b-form" records):
+// Site-record geometry.  A record holds the blocks a_00 and a_01 (16 bytes per
+// complex entry) and then the phase entry r.  FP64 records hold each value once as
+// (re, im).  The FP32 formats hold two forms of every record, in two arrays (all
+// row-side "a-form" records of the buffer first, then all column-side "b-form"
+// records):
 //   a-form entry (A, iA)              = (re, im, -im, re)
 //   b-form entry (conj B, i conj B)   = (re, -im, im, re)
 // so that a complex multiply-accumulate is two packed FP32x2 FMAs with one
 // broadcast operand:  E A = E.re * A + E.im * (iA),  X conj(B) = X.re * conj(B) + X.im * (i conj(B)).
-// Split FP32 stores, per block, the hi entries then the lo entries, each in form.
+// Split FP32 stores, per block, the hi entries then the lo entries, each in
+// form, and the phase as a hi entry then a lo entry.
 template <int CHI, int PREC>
 struct Record {
   static constexpr int H = CHI / 2;                    // block side
   static constexpr int kEntries = H * H;               // complex entries per block
   static constexpr int kForms = (PREC == QSVM_FP64) ? 1 : 2;
   static constexpr int kEntryBytes = 16;               // (re, im) double, or one form entry of 4 floats
+  static constexpr int kParts = (PREC == QSVM_FP32_SPLIT) ? 2 : 1;
   static constexpr int kPartBytes = kEntries * kEntryBytes;
-  static constexpr int kBlockBytes = kPartBytes * (PREC == QSVM_FP32_SPLIT ? 2 : 1);
-  static constexpr int kBytes = 4 * kBlockBytes;       // one form of one site
+  static constexpr int kBlockBytes = kPartBytes * kParts;
+  static constexpr int kPhaseOff = 2 * kBlockBytes;    // phase r: one entry per part
+  static constexpr int kBytes = kPhaseOff + kParts * kEntryBytes;  // one form of one site
 };
 
-inline size_t record_bytes(int chi, int prec) {
-  const size_t h2 = (size_t)(chi / 2) * (chi / 2);
-  return 4 * h2 * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1);
+__host__ __device__ constexpr size_t record_bytes(int chi, int prec) {
+  return (2 * (size_t)(chi / 2) * (chi / 2) + 1) * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1);
 }
+static_assert(record_bytes(4, QSVM_FP64) == Record<4, QSVM_FP64>::kBytes, "record geometry");
+static_assert(record_bytes(2, QSVM_FP32) == Record<2, QSVM_FP32>::kBytes, "record geometry");
+static_assert(record_bytes(8, QSVM_FP32_SPLIT) == Record<8, QSVM_FP32_SPLIT>::kBytes, "record geometry");
+static_assert(Record<4, QSVM_FP32_SPLIT>::kBytes % 16 == 0 && Record<2, QSVM_FP64>::kBytes % 16 == 0,
+              "bulk copies move whole 16-byte units");
 inline int record_forms(int prec) { return prec == QSVM_FP64 ? 1 : 2; }
 
 // ---- tile order --------------------------------------------------------------
@@ -119,8 +130,8 @@ struct TileArgs {
 struct PipeCfg {
   int S;            // sites per chunk
   int stages;       // 2..4
-  int slot_bytes;   // S * record bytes + 16 (per point per stage)
-  int stage_bytes;  // 32 points * slot_bytes
+  int slot_bytes;   // S * record bytes, padded to an odd number of 16-byte units (per point per stage)
+  int stage_bytes;  // 2 * tile side points * slot_bytes
 };
 
 // One Gram job of a batch, as the persistent kernel reads it (64 bytes).

@@ -18,15 +18,16 @@ def test_exports_every_declared_symbol():
 
 
 def test_record_and_mps_bytes():
-    # chi^2 complex entries per site (half of the dense 2 chi^2 are structural zeros),
-    # 16 bytes each; split FP32 holds hi and lo; FP32 formats hold two forms
+    # per site the blocks a_00, a_01 (chi^2 / 2 complex entries) and the phase r, 16 bytes
+    # each; split FP32 holds hi and lo; FP32 formats hold two forms
     for reps, chi in ((1, 2), (2, 4), (3, 8)):
-        assert qsvm.qsvm_mps_record_bytes(reps, "fp64") == chi * chi * 16
-        assert qsvm.qsvm_mps_record_bytes(reps, "fp32") == chi * chi * 16
-        assert qsvm.qsvm_mps_record_bytes(reps, "fp32_split") == chi * chi * 32
-    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp64") == 8192 * 784 * 256
-    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32") == 2 * 8192 * 784 * 256
-    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 2 * 8192 * 784 * 512
+        entries = 2 * (chi // 2) ** 2 + 1  # blocks a_00, a_01 and the phase r
+        assert qsvm.qsvm_mps_record_bytes(reps, "fp64") == entries * 16
+        assert qsvm.qsvm_mps_record_bytes(reps, "fp32") == entries * 16
+        assert qsvm.qsvm_mps_record_bytes(reps, "fp32_split") == entries * 32
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp64") == 8192 * 784 * 144
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32") == 2 * 8192 * 784 * 144
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 2 * 8192 * 784 * 288
     assert qsvm.qsvm_mps_record_bytes(4, "fp64") == 0
     assert qsvm.qsvm_mps_record_bytes(2, 7) == 0
 
@@ -133,7 +134,7 @@ def test_configs():
                 S, st = qsvm.qsvm_config_info(c, reps, prec)
                 assert S >= 1 and 2 <= st <= 4
     S2, _ = qsvm.qsvm_config_info(1, 2, "fp32_split")
-    assert S2 == 2  # 1 KB of 512-byte records per point and chunk
+    assert S2 == 3  # 1 KB of 288-byte records per point and chunk
     assert qsvm.qsvm_get_config(2, "fp64") == -1
     qsvm.qsvm_set_config(2, "fp64", 0)
     assert qsvm.qsvm_get_config(2, "fp64") == 0

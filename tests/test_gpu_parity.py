@@ -33,16 +33,21 @@ def _dev(X):
 
 
 def _decode_fp64(buf, N, n, reps):
-    """Site tensors A[i, k, sigma, t, u] from FP64 records (layout of include/qsvm.h)."""
+    """Site tensors A[i, k, sigma, t, u] from FP64 records (layout of include/qsvm.h):
+    blocks a_0s[q][p] = A[s][2q][2p+s], then r; the rows with c = 1 are a_1s = r_s a_0s
+    with r_0 = r, r_1 = conj(r)."""
     chi = 2 ** reps
     H = chi // 2
-    raw = buf.cpu().numpy().view(np.complex128).reshape(N, n, 4, H, H)
+    raw = buf.cpu().numpy().view(np.complex128).reshape(N, n, 2 * H * H + 1)
+    r = raw[:, :, 2 * H * H]
     A = np.zeros((N, n, 2, chi, chi), complex)
-    for c in range(2):
-        for s in range(2):
-            for qq in range(H):
-                for p in range(H):
-                    A[:, :, s, 2 * qq + c, 2 * p + s] = raw[:, :, 2 * c + s, qq, p]
+    for s in range(2):
+        a0 = raw[:, :, s * H * H:(s + 1) * H * H].reshape(N, n, H, H)
+        rs = r if s == 0 else np.conj(r)
+        for qq in range(H):
+            for p in range(H):
+                A[:, :, s, 2 * qq, 2 * p + s] = a0[:, :, qq, p]
+                A[:, :, s, 2 * qq + 1, 2 * p + s] = rs * a0[:, :, qq, p]
     return A
 
 
@@ -88,9 +93,10 @@ def test_build_mps_lowprec_formats(q):
     N, n, reps = 5, 33, 2
     X = inputs.mnist_like_features(N, n, 77)
     d = _dev(X)
-    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, 4, 4)
-    f32 = q.qsvm_build_mps(d, reps, "fp32").cpu().numpy().view(np.float32).reshape(2, N * n, 4, 4, 4)
-    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(2, N * n, 4, 2, 4, 4)
+    E = 9  # entries per record: two 2 x 2 blocks and the phase
+    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, E)
+    f32 = q.qsvm_build_mps(d, reps, "fp32").cpu().numpy().view(np.float32).reshape(2, N * n, E, 4)
+    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(2, N * n, 2 * E, 4)
 
     def check_forms(a, b):  # a-form (re, im, -im, re); b-form (re, -im, im, re)
         re, im = a[..., 0], a[..., 1]
@@ -100,12 +106,22 @@ def test_build_mps_lowprec_formats(q):
         return re.astype(np.float64) + 1j * im.astype(np.float64)
 
     v32 = check_forms(f32[0], f32[1])
-    assert np.array_equal(v32, f64.astype(np.complex64).astype(np.complex128))
-    hi = check_forms(spl[0, :, :, 0], spl[1, :, :, 0])
-    lo = check_forms(spl[0, :, :, 1], spl[1, :, :, 1])
+    # FP32 records are the FP64 values rounded to float (within half an ulp, plus
+    # slack for the 1e-17 noise the two builds may carry in entries that are 0)
+    for a, b in ((v32.real, f64.real), (v32.imag, f64.imag)):
+        assert np.all(np.abs(a - b) <= np.abs(b) * 2.0 ** -24 + 1e-15)
+    # split: per block 4 hi entries then 4 lo entries; then the phase's hi and lo entry
+    hi_idx = [0, 1, 2, 3, 8, 9, 10, 11, 16]
+    lo_idx = [4, 5, 6, 7, 12, 13, 14, 15, 17]
+    hi = check_forms(spl[0][:, hi_idx], spl[1][:, hi_idx])
+    lo = check_forms(spl[0][:, lo_idx], spl[1][:, lo_idx])
     for part in (hi.real, hi.imag):
         assert np.array_equal(np.round(part * 2048) / 2048, part)
     assert np.max(np.abs(hi + lo - f64)) <= 2 ** -34
+    # the phase entry is exp(2 i theta_{k-1}) (1 at site 0)
+    theta = (np.pi - X[:, :-1]) * (np.pi - X[:, 1:])
+    r = np.concatenate([np.ones((N, 1)), np.exp(2j * theta)], axis=1).reshape(-1)
+    assert np.max(np.abs(f64[:, 8] - r)) <= 1e-14
 
 
 # ----------------------------------------------------------- small Grams ---
