@@ -71,15 +71,22 @@ enum qsvm_precision {
  * The feature map ends with a diagonal layer, so the physical index of site k
  * equals the last-repetition spin carried on its right bond: with the right
  * bond index u = 2p + s and left bond index t = 2q + c, the tensor
- * A_k[sigma][t][u] is nonzero only when sigma == s.  A site record stores the
- * four chi/2 x chi/2 blocks a_cs[q][p] = A_k[s][2q+c][2p+s], block index
- * b = 2c + s, each row-major over (q, p), 16 bytes per entry:
+ * A_k[sigma][t][u] is nonzero only when sigma == s.  The left bit c (the left
+ * neighbour's last-repetition spin) enters only through the last repetition's
+ * ZZ phase, so the blocks a_cs[q][p] = A_k[s][2q+c][2p+s] satisfy
+ * a_1s = r_s a_0s with r_0 = exp(2 i theta_{k-1}) and r_1 = conj(r_0)
+ * (theta_{k-1} = (pi - x_{k-1})(pi - x_k); r = 1 at site 0).  A site record
+ * stores the two chi/2 x chi/2 blocks a_00, a_01, each row-major over (q, p),
+ * then the phase r, 16 bytes per complex value:
  *   QSVM_FP64        (re, im) as two doubles;
  *   QSVM_FP32        one "form" entry of four floats (below);
  *   QSVM_FP32_SPLIT  per block: the chi^2/4 "hi" form entries (re and im on the
- *                    2^-11 grid), then the chi^2/4 "lo" form entries.
- * qsvm_mps_record_bytes() is the size of one record.  FP64 buffers hold one
- * record per (point, site), point-major: record (i, k) at byte
+ *                    2^-11 grid), then the chi^2/4 "lo" form entries; the phase
+ *                    as a hi entry then a lo entry.
+ * qsvm_mps_record_bytes() is the size of one record: (chi^2/2 + 1) x 16 bytes,
+ * twice that for QSVM_FP32_SPLIT, where at reps = 3 each block is also followed
+ * by 16 unused bytes (shared-memory bank spreading).  FP64 buffers hold one record per
+ * (point, site), point-major: record (i, k) at byte
  * (i * n_qubits + k) * record_bytes.  The FP32 formats hold two forms of every
  * record in two consecutive arrays of that layout: first the row-side a-form,
  * entry (re, im, -im, re) = (A, iA); then the column-side b-form, entry

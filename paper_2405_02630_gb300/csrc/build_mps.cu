@@ -35,9 +35,9 @@ struct cd {
 };
 __device__ __forceinline__ cd cmul(cd a, cd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 
-// Store one complex entry (q, p) of block b, in the requested format: FP64 once
-// as (re, im); FP32 formats in both forms (recA: a-form (A, iA); recB: b-form
-// (conj A, i conj A)), the split format as hi then lo parts of each block.
+// Store one complex value at byte offset off of a record, in the requested
+// format: FP64 once as (re, im); FP32 formats in both forms (recA: a-form
+// (A, iA); recB: b-form (conj A, i conj A)), the split format as hi then lo parts.
 __device__ __forceinline__ void store_forms(uint8_t* pa, uint8_t* pb, float re, float im) {
   reinterpret_cast<float4*>(pa)[0] = make_float4(re, im, -im, re);
   reinterpret_cast<float4*>(pb)[0] = make_float4(re, -im, im, re);
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
       cd val;
       if (last) val = (u < 2) ? v[u][0] : cd{0.0, 0.0};
       else val = v[s][u];
-      store_entry<CHI, PREC>(recA, recB, s * Rec::kBlockBytes + (q * H + p) * Rec::kEntryBytes, val);
+      store_entry<CHI, PREC>(recA, recB, s * Rec::kBlockStride + (q * H + p) * Rec::kEntryBytes, val);
     }
   }
   // r = exp(2 i theta) = (zzm)^2: the ratio of the c = 1 rows to the c = 0 rows for sigma = 0

@@ -89,8 +89,8 @@ struct Engine<CHI, QSVM_FP64> {
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       double2 a[H][H], b[H][H];
-      load_block_d<H>(ra + s * Rec::kBlockBytes, a);
-      load_block_d<H>(rb + s * Rec::kBlockBytes, b);
+      load_block_d<H>(ra + s * Rec::kBlockStride, a);
+      load_block_d<H>(rb + s * Rec::kBlockStride, b);
       double2 X[H][H];
 #pragma unroll
       for (int p = 0; p < H; ++p)
@@ -241,8 +241,8 @@ struct Engine<CHI, QSVM_FP32> {
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       float2 A[H][H], iA[H][H], cB[H][H], icB[H][H];
-      load_forms<H>(ra + s * Rec::kBlockBytes, A, iA);
-      load_forms<H>(rb + s * Rec::kBlockBytes, cB, icB);
+      load_forms<H>(ra + s * Rec::kBlockStride, A, iA);
+      load_forms<H>(rb + s * Rec::kBlockStride, cB, icB);
       float2 X[H][H];
 #pragma unroll
       for (int p = 0; p < H; ++p)
@@ -394,8 +394,8 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
     float2 Nh[2][H][H], Nl[2][H][H];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const uint32_t pa = ra + s * Rec::kBlockBytes;
-      const uint32_t pb = rb + s * Rec::kBlockBytes;
+      const uint32_t pa = ra + s * Rec::kBlockStride;
+      const uint32_t pb = rb + s * Rec::kBlockStride;
       float2 Ah[H][H], iAh[H][H], Al[H][H], iAl[H][H];
       float2 Bh[H][H], iBh[H][H], Bl[H][H], iBl[H][H];  // conj(b) and i conj(b), hi and lo
       load_forms<H>(pa, Ah, iAh);
@@ -524,7 +524,7 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
   static constexpr int GX = grid_x(CHI);
   static constexpr int kRenormEvery = 1;
   using Rec = Record<CHI, QSVM_FP32_SPLIT>;
-  float* ebuf;     // this pair's environment: entry (c, q, r) at (c*16 + q*4 + r) * 4 floats: hi.re, hi.im, lo.re, lo.im
+  float* ebuf;     // this pair's environment: 32 swizzled entries (see entry()) of hi.re, hi.im, lo.re, lo.im
   int s, h;        // block of E' and row pair this thread owns
   unsigned mask;   // the warp's active mask (all 32 lanes run the site loop together)
   int L;
@@ -539,14 +539,18 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
     for (int p = 0; p < 2; ++p)
       for (int r = 0; r < H; ++r) {
         const int q = 2 * h + p;
-        float4* e = reinterpret_cast<float4*>(ebuf + (s * 16 + q * 4 + r) * 4);
-        *e = make_float4((s == 0 && q == 0 && r == 0) ? 1.f : 0.f, 0.f, 0.f, 0.f);
+        *entry(s, q, r) = make_float4((s == 0 && q == 0 && r == 0) ? 1.f : 0.f, 0.f, 0.f, 0.f);
       }
     __syncwarp(mask);
   }
 
+  // Entry (c, q, r) of the pair's environment.  A 16-byte access is served a
+  // quarter-warp (two pairs) at a time; swizzling r by (2c + q/2) puts the four
+  // threads of a quad in four different 16-byte bank groups whenever they touch
+  // the same (q & 1, r) in different blocks or row pairs, and the pair stride
+  // (36 entries, 4 mod 8) moves the quarter-warp's other pair to the other four.
   __device__ __forceinline__ float4* entry(int c, int q, int r) const {
-    return reinterpret_cast<float4*>(ebuf + (c * 16 + q * 4 + r) * 4);
+    return reinterpret_cast<float4*>(ebuf + (c * 16 + q * 4 + (r ^ (2 * c + (q >> 1)))) * 4);
   }
 
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
@@ -574,8 +578,8 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
 #pragma unroll
       for (int r = 0; r < H; ++r) *entry(s, 2 * h + j, r) = Gq[j][r];
     __syncwarp(mask);  // G_0 and G_1 are complete
-    const uint32_t pa = ra + s * Rec::kBlockBytes;
-    const uint32_t pb = rb + s * Rec::kBlockBytes;
+    const uint32_t pa = ra + s * Rec::kBlockStride;
+    const uint32_t pb = rb + s * Rec::kBlockStride;
     // X[p][r] = sum_q a[q][p] G_s[q][r] for the thread's two rows p
     float2 Xh[2][H], Xl[2][H], Xf[2][H];
     {
@@ -712,8 +716,9 @@ __host__ __device__ constexpr int threads_per_pair(int chi, int prec) {
 }
 __host__ __device__ constexpr int tile_side(int chi, int prec) { return threads_per_pair(chi, prec) == 4 ? 8 : 16; }
 __host__ __device__ constexpr int out_bytes(int ti) { return ti * (ti + 1) * 16; }
-// shared environment buffer of the four-thread layout: 32 entries x 16 B per pair, +16 B
-constexpr int kQuadPairFloats = 32 * 4 + 4;
+// shared environment buffer of the four-thread layout: 32 entries x 16 B per pair,
+// padded to 36 entries (a stride of 4 mod 8 sixteen-byte bank groups)
+constexpr int kQuadPairFloats = 36 * 4;
 __host__ __device__ constexpr int ebuf_bytes(int chi, int prec) {
   return threads_per_pair(chi, prec) == 4 ? (kTileThreads / 4) * kQuadPairFloats * 4 : 0;
 }

@@ -45,16 +45,23 @@ struct Record {
   static constexpr int kParts = (PREC == QSVM_FP32_SPLIT) ? 2 : 1;
   static constexpr int kPartBytes = kEntries * kEntryBytes;
   static constexpr int kBlockBytes = kPartBytes * kParts;
-  static constexpr int kPhaseOff = 2 * kBlockBytes;    // phase r: one entry per part
+  // Split FP32 at chi = 8 is read by four threads per pair, which load the same
+  // entry of both blocks at once: 16 bytes between the blocks put those reads in
+  // different shared-memory bank groups.
+  static constexpr int kBlockStride = kBlockBytes + ((CHI >= 8 && PREC == QSVM_FP32_SPLIT) ? 16 : 0);
+  static constexpr int kPhaseOff = 2 * kBlockStride;   // phase r: one entry per part
   static constexpr int kBytes = kPhaseOff + kParts * kEntryBytes;  // one form of one site
 };
 
 __host__ __device__ constexpr size_t record_bytes(int chi, int prec) {
-  return (2 * (size_t)(chi / 2) * (chi / 2) + 1) * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1);
+  return (2 * (size_t)(chi / 2) * (chi / 2) + 1) * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1) +
+         ((chi >= 8 && prec == QSVM_FP32_SPLIT) ? 32 : 0);
 }
 static_assert(record_bytes(4, QSVM_FP64) == Record<4, QSVM_FP64>::kBytes, "record geometry");
 static_assert(record_bytes(2, QSVM_FP32) == Record<2, QSVM_FP32>::kBytes, "record geometry");
 static_assert(record_bytes(8, QSVM_FP32_SPLIT) == Record<8, QSVM_FP32_SPLIT>::kBytes, "record geometry");
+static_assert(record_bytes(4, QSVM_FP32_SPLIT) == Record<4, QSVM_FP32_SPLIT>::kBytes, "record geometry");
+static_assert(record_bytes(8, QSVM_FP64) == Record<8, QSVM_FP64>::kBytes, "record geometry");
 static_assert(Record<4, QSVM_FP32_SPLIT>::kBytes % 16 == 0 && Record<2, QSVM_FP64>::kBytes % 16 == 0,
               "bulk copies move whole 16-byte units");
 inline int record_forms(int prec) { return prec == QSVM_FP64 ? 1 : 2; }

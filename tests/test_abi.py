@@ -24,7 +24,8 @@ def test_record_and_mps_bytes():
         entries = 2 * (chi // 2) ** 2 + 1  # blocks a_00, a_01 and the phase r
         assert qsvm.qsvm_mps_record_bytes(reps, "fp64") == entries * 16
         assert qsvm.qsvm_mps_record_bytes(reps, "fp32") == entries * 16
-        assert qsvm.qsvm_mps_record_bytes(reps, "fp32_split") == entries * 32
+        pad = 32 if chi == 8 else 0  # 16 bytes after each block of the four-thread layout
+        assert qsvm.qsvm_mps_record_bytes(reps, "fp32_split") == entries * 32 + pad
     assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp64") == 8192 * 784 * 144
     assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32") == 2 * 8192 * 784 * 144
     assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 2 * 8192 * 784 * 288
