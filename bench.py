@@ -67,6 +67,12 @@ def dense_cmacs_per_entry(n: int, reps: int) -> int:
 # real FP32 FMAs each arithmetic issues per complex MAC of the contraction
 FMA_PER_CMAC = {"fp32": 4, "fp32_split": 12, "fp64": 4}
 
+# DRAM bytes (read + write) of one pair-kernel launch, from one ncu capture of the
+# same configuration with the default pipeline shape (dram__bytes_read.sum +
+# dram__bytes_write.sum; profiles/pair_tile_split_n784_r2.md).  Configurations
+# not captured with the current kernel report null.
+MEASURED_TRAFFIC_BYTES = {("gram_n784_r2_N8192", "fp32_split"): 73_988_679_680 + 563_192_832}
+
 
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -320,7 +326,9 @@ def run_ours(args):
         bound = "alu"
     fma_frac = (FMA_PER_CMAC[prec] * 2.0 * cm * pairs_rank / (kms * 1e-3) / 1e12) / peak
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"pair_tile_kernel<chi={2 ** reps},{prec}>",
+                "traffic": MEASURED_TRAFFIC_BYTES.get((args.workload, prec)) if world == 1 else None,
+                "traffic_unit": "bytes per launch (ncu)",
+                "kernel": f"pair_tile_kernel<chi={2 ** reps},{prec}>",
                 "peak_basis": (f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x 2 x {mhz:.0f} MHz"
                                if prec != "fp64" else "nominal FP64 1.25 TFLOP/s"),
                 "algorithmic_flops_per_entry": 8 * cm,

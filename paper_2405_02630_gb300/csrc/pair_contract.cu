@@ -6,18 +6,24 @@
 namespace qsvm {
 
 // Candidate pipeline shapes the autotuner chooses from: bytes of site records per
-// point and chunk, and stages in flight.  Index 1 is the default.
+// point and chunk, and stages in flight (default_shape() picks per chi and precision).
 struct PipeShape {
   int chunk_bytes;
   int stages;
 };
-static const PipeShape kShapes[] = {{512, 4}, {1024, 3}, {512, 3}, {1024, 2}, {1024, 4}, {2048, 2}, {2048, 3}, {512, 2}};
+static const PipeShape kShapes[] = {{512, 4},  {1024, 3}, {512, 3},  {1024, 2}, {1024, 4},
+                                    {2048, 2}, {2048, 3}, {512, 2},  {1152, 2}, {1440, 2}};
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 
-// Defaults from autotuner runs on one GB300 (n = 784 Grams): plain FP32 and the
-// chi = 8 kernels gain a resident CTA per SM with two stages; split FP32 at
-// chi <= 4 is fastest with three stages of 1 KB chunks.
-int default_shape(int chi, int prec) { return (prec == QSVM_FP32 || chi >= 8) ? 3 : 1; }
+// Defaults from shape sweeps on one GB300 (n = 784, N = 8192 Grams): plain FP32
+// and the chi = 8 kernels run best with two stages of 1 KB chunks (7 FP32 sites);
+// split FP32 at chi <= 4 with two stages of five sites (634 ms against 660 ms
+// for three stages of three), which keeps two CTAs per SM and pays the per-chunk
+// wait and hand-off less often.
+int default_shape(int chi, int prec) {
+  if (prec == QSVM_FP32_SPLIT && chi <= 4) return 9;
+  return (prec == QSVM_FP32 || chi >= 8) ? 3 : 1;
+}
 
 int num_pipe_shapes() { return kNumShapes; }
 
