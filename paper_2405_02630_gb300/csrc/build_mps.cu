@@ -113,6 +113,36 @@ __device__ __forceinline__ void site_row(int t, bool has_left, cd rz0, cd zzp, c
   }
 }
 
+// Phase-form record (reps = 2).  Multiplying out the gates of one site gives
+// A^s[2q+c][2p+s] = (1/2) (-1)^{p s} e^{-i x (z(p) + z(s))} e^{-i theta (z(q) z(p) + z(c) z(s))}
+// (z(b) = 1 - 2b; the two RZ layers, the two ZZ layers with the left neighbour's
+// layer spins q, c, and the Hadamard sign between the layers), so with
+// P = e^{-i x_k}, T = e^{-i theta_{k-1}} every entry is +-1/2 times one of 1,
+// T^2, P^2, P^2 T^2 or a conjugate: the record keeps those three phases, each
+// evaluated directly from its angle.  The last site keeps the same tensor with
+// its right bond open (the contraction sums it at the end).
+template <int PREC>
+__device__ __forceinline__ void store_phase(uint8_t* rec, int v, cd z) {
+  using Rec = Record<4, PREC>;
+  if constexpr (PREC == QSVM_FP64) {
+    reinterpret_cast<double2*>(rec + Rec::off(v, 0, 0))[0] = make_double2(z.re, z.im);
+  } else if constexpr (PREC == QSVM_FP32) {
+    store_forms(rec + Rec::off(v, 0, 0), rec + Rec::off(v, 1, 0), __double2float_rn(z.re), __double2float_rn(z.im));
+  } else {
+    constexpr double sc = (double)(1 << kGridT);
+    const double hr = rint(z.re * sc) / sc, hi = rint(z.im * sc) / sc;
+    store_forms(rec + Rec::off(v, 0, 0), rec + Rec::off(v, 1, 0), (float)hr, (float)hi);
+    store_forms(rec + Rec::off(v, 0, 1), rec + Rec::off(v, 1, 1), __double2float_rn(z.re - hr),
+                __double2float_rn(z.im - hi));
+  }
+}
+
+__device__ __forceinline__ cd unit_phase(double a) {  // e^{-i a}
+  double sn, cs;
+  sincos(a, &sn, &cs);
+  return cd{cs, -sn};
+}
+
 template <int R, int PREC>
 __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict__ X, int64_t n_points, int n,
                                                         uint8_t* __restrict__ mps) {
@@ -123,45 +153,53 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
   const int64_t i = gid / n;
   const int k = (int)(gid - i * n);
   const double xk = X[i * n + k];
-  double sx, cx;
-  sincos(xk, &sx, &cx);
-  const cd rz0 = cd{cx, -sx};  // e^{-i x_k}
-  cd zzp = cd{1.0, 0.0}, zzm = cd{1.0, 0.0};
-  const bool has_left = k > 0;
-  if (has_left) {
-    const double th = (kPi - X[i * n + k - 1]) * (kPi - xk);
-    double st, ct;
-    sincos(th, &st, &ct);
-    zzp = cd{ct, -st};  // a = 0: z(a) = +1 -> exp(-i theta) for sigma = 0
-    zzm = cd{ct, st};   // a = 1: z(a) = -1 -> exp(+i theta) for sigma = 0
-  }
-  uint8_t* recA = mps + gid * Rec::kBytes;
-  uint8_t* recB = recA + (Rec::kForms == 2 ? n_points * (int64_t)n * Rec::kBytes : 0);
-  const bool last = (k == n - 1);
-  constexpr int H = CHI / 2;
-  // rows t = 2q (c = 0) of both blocks s
-  for (int q = 0; q < H; ++q) {
-    const int t = 2 * q;
-    cd v[2][CHI];
-    if (!has_left && t > 0) {
-#pragma unroll
-      for (int u = 0; u < CHI; ++u) v[0][u] = v[1][u] = cd{0.0, 0.0};
-    } else if (last) {
-      site_row<R, true>(t, has_left, rz0, zzp, zzm, v);
-    } else {
-      site_row<R, false>(t, has_left, rz0, zzp, zzm, v);
+  if constexpr (R == 2) {
+    const double th = k > 0 ? (kPi - X[i * n + k - 1]) * (kPi - xk) : 0.0;
+    uint8_t* rec = mps + gid * Record<4, PREC>::kBytes;
+    store_phase<PREC>(rec, 0, unit_phase(2.0 * th));
+    store_phase<PREC>(rec, 1, unit_phase(2.0 * xk));
+    store_phase<PREC>(rec, 2, unit_phase(2.0 * (xk + th)));
+  } else {
+    double sx, cx;
+    sincos(xk, &sx, &cx);
+    const cd rz0 = cd{cx, -sx};  // e^{-i x_k}
+    cd zzp = cd{1.0, 0.0}, zzm = cd{1.0, 0.0};
+    const bool has_left = k > 0;
+    if (has_left) {
+      const double th = (kPi - X[i * n + k - 1]) * (kPi - xk);
+      double st, ct;
+      sincos(th, &st, &ct);
+      zzp = cd{ct, -st};  // a = 0: z(a) = +1 -> exp(-i theta) for sigma = 0
+      zzm = cd{ct, st};   // a = 1: z(a) = -1 -> exp(+i theta) for sigma = 0
     }
+    uint8_t* recA = mps + gid * Rec::kBytes;
+    uint8_t* recB = recA + (Rec::kForms == 2 ? n_points * (int64_t)n * Rec::kBytes : 0);
+    const bool last = (k == n - 1);
+    constexpr int H = CHI / 2;
+    // rows t = 2q (c = 0) of both blocks s
+    for (int q = 0; q < H; ++q) {
+      const int t = 2 * q;
+      cd v[2][CHI];
+      if (!has_left && t > 0) {
 #pragma unroll
-    for (int u = 0; u < CHI; ++u) {
-      const int s = u & 1, p = u >> 1;
-      cd val;
-      if (last) val = (u < 2) ? v[u][0] : cd{0.0, 0.0};
-      else val = v[s][u];
-      store_entry<CHI, PREC>(recA, recB, s * Rec::kBlockStride + (q * H + p) * Rec::kEntryBytes, val);
+        for (int u = 0; u < CHI; ++u) v[0][u] = v[1][u] = cd{0.0, 0.0};
+      } else if (last) {
+        site_row<R, true>(t, has_left, rz0, zzp, zzm, v);
+      } else {
+        site_row<R, false>(t, has_left, rz0, zzp, zzm, v);
+      }
+#pragma unroll
+      for (int u = 0; u < CHI; ++u) {
+        const int s = u & 1, p = u >> 1;
+        cd val;
+        if (last) val = (u < 2) ? v[u][0] : cd{0.0, 0.0};
+        else val = v[s][u];
+        store_entry<CHI, PREC>(recA, recB, s * Rec::kBlockStride + (q * H + p) * Rec::kEntryBytes, val);
+      }
     }
+    // r = exp(2 i theta) = (zzm)^2: the ratio of the c = 1 rows to the c = 0 rows for sigma = 0
+    store_entry<CHI, PREC>(recA, recB, Rec::kPhaseOff, cmul(zzm, zzm));
   }
-  // r = exp(2 i theta) = (zzm)^2: the ratio of the c = 1 rows to the c = 0 rows for sigma = 0
-  store_entry<CHI, PREC>(recA, recB, Rec::kPhaseOff, cmul(zzm, zzm));
 }
 
 template <int R, int PREC>

@@ -151,8 +151,8 @@ struct Engine<CHI, QSVM_FP64> {
   }
 
   __device__ __forceinline__ void amplitude(double& re, double& im) const {
-    re = E[0][0][0].x + E[1][0][0].x;
-    im = E[0][0][0].y + E[1][0][0].y;
+    re = __dadd_rn(E[0][0][0].x, E[1][0][0].x);
+    im = __dadd_rn(E[0][0][0].y, E[1][0][0].y);
   }
 };
 
@@ -296,8 +296,8 @@ struct Engine<CHI, QSVM_FP32> {
   }
 
   __device__ __forceinline__ void amplitude(double& re, double& im) const {
-    re = (double)E[0][0][0].x + (double)E[1][0][0].x;
-    im = (double)E[0][0][0].y + (double)E[1][0][0].y;
+    re = __dadd_rn((double)E[0][0][0].x, (double)E[1][0][0].x);
+    im = __dadd_rn((double)E[0][0][0].y, (double)E[1][0][0].y);
   }
 };
 
@@ -320,13 +320,15 @@ struct Engine<CHI, QSVM_FP32> {
 // else is rounded.  This is the split hi+lo compensated product carried out on
 // the FP32 pipe: 6 packed FMAs (12 FMAs) per complex MAC.
 
-// rho_s = r_s(i) conj(r_s(j)) as split forms: R[s] = rho_s, iR[s] = i rho_s (hi and lo).
-__device__ __forceinline__ void split_phase(uint32_t pa, uint32_t pb, float2 (&Rh)[2], float2 (&iRh)[2],
-                                            float2 (&Rl)[2], float2 (&iRl)[2]) {
-  const float4 ih = *reinterpret_cast<const float4*>(sptr(pa));
-  const float4 il = *reinterpret_cast<const float4*>(sptr(pa + 16));
-  const float4 jh = *reinterpret_cast<const float4*>(sptr(pb));
-  const float4 jl = *reinterpret_cast<const float4*>(sptr(pb + 16));
+// u conj(w) for split values given as u's a-form entries (hi at ah, lo at al) and
+// w's b-form entries (hi at bh, lo at bl), returned as the split forms of both
+// rho_0 = u conj(w) and rho_1 = conj(rho_0): R[s] = rho_s, iR[s] = i rho_s.
+__device__ __forceinline__ void split_phase(uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl, float2 (&Rh)[2],
+                                            float2 (&iRh)[2], float2 (&Rl)[2], float2 (&iRl)[2]) {
+  const float4 ih = *reinterpret_cast<const float4*>(sptr(ah));
+  const float4 il = *reinterpret_cast<const float4*>(sptr(al));
+  const float4 jh = *reinterpret_cast<const float4*>(sptr(bh));
+  const float4 jl = *reinterpret_cast<const float4*>(sptr(bl));
   const float2 cjh = make_float2(jh.x, jh.y), icjh = make_float2(jh.z, jh.w);
   const float2 cjl = make_float2(jl.x, jl.y), icjl = make_float2(jl.z, jl.w);
   const float2 h = fma2(bc(ih.x), cjh, mul2(bc(ih.y), icjh));  // exact
@@ -345,13 +347,14 @@ __device__ __forceinline__ void split_phase(uint32_t pa, uint32_t pb, float2 (&R
   iRl[1] = make_float2(rl.y, rl.x);
 }
 
-// G = E_0 + rho E_1 split onto the 2^-kGridG grid (hi, lo, full).
+// G = E_0 + rho E_1 split onto the 2^-GG grid (hi, lo, full).
+template <int GG = kGridG>
 __device__ __forceinline__ void split_mix(float2 e0h, float2 e0l, float2 e1h, float2 e1l, float2 e1f, float2 Rh,
                                           float2 iRh, float2 Rl, float2 iRl, float2& gh, float2& gl, float2& gf) {
   const float2 h = fma2(bc(e1h.y), iRh, fma2(bc(e1h.x), Rh, e0h));  // exact
   const float2 l = fma2(bc(e1f.y), iRl, fma2(bc(e1f.x), Rl, fma2(bc(e1l.y), iRh, fma2(bc(e1l.x), Rh, e0l))));
   const float2 v = add2(h, l);
-  gh = grid_round2<kGridG>(v);
+  gh = grid_round2<GG>(v);
   gl = add2(fma2(gh, make_float2(-1.f, -1.f), h), l);  // (h - gh) is exact
   gf = v;
 }
@@ -379,7 +382,8 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     const float2 m1 = make_float2(-1.f, -1.f);
     float2 Rh[2], iRh[2], Rl[2], iRl[2];
-    split_phase(ra + Rec::kPhaseOff, rb + Rec::kPhaseOff, Rh, iRh, Rl, iRl);
+    split_phase(ra + Rec::kPhaseOff, ra + Rec::kPhaseOff + 16, rb + Rec::kPhaseOff, rb + Rec::kPhaseOff + 16, Rh, iRh,
+                Rl, iRl);
     // G_s = E_0 + rho_s E_1, in place of E_s
 #pragma unroll
     for (int q = 0; q < H; ++q)
@@ -496,8 +500,451 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
   __device__ __forceinline__ void renorm() {}
 
   __device__ __forceinline__ void amplitude(double& re, double& im) const {
-    re = ((double)Eh[0][0][0].x + (double)El[0][0][0].x) + ((double)Eh[1][0][0].x + (double)El[1][0][0].x);
-    im = ((double)Eh[0][0][0].y + (double)El[0][0][0].y) + ((double)Eh[1][0][0].y + (double)El[1][0][0].y);
+    re = __dadd_rn(__dadd_rn((double)Eh[0][0][0].x, (double)El[0][0][0].x),
+                   __dadd_rn((double)Eh[1][0][0].x, (double)El[1][0][0].x));
+    im = __dadd_rn(__dadd_rn((double)Eh[0][0][0].y, (double)El[0][0][0].y),
+                   __dadd_rn((double)Eh[1][0][0].y, (double)El[1][0][0].y));
+  }
+};
+
+// ------------------------------------------------ phase form (reps = 2) ----
+// The row point's blocks, unscaled (their factors 1/2 go to the log scale:
+// L -= 2 per site), with V0 = T^2, V1 = P^2, V2 = P^2 T^2 (rows q, columns p):
+//   a_00 = [[V2, 1], [V1, V0]],   a_01 = [[1, -conj(V2)], [conj(V0), -conj(V1)]].
+// The column point's phases are W0, W1, W2.  Per site:
+//   rho_0 = W0 conj(V0) (= r(i) conj(r(j)) with r = conj(T^2)),  rho_1 = conj(rho_0),
+//   G_s = E_0 + rho_s E_1;
+//   s = 0:  X[0][r] = V2 G[0][r] + V1 G[1][r],      X[1][r] = G[0][r] + V0 G[1][r],
+//           E'[p][0] = X[p][0] conj(W2) + X[p][1] conj(W1),   E'[p][1] = X[p][0] + X[p][1] conj(W0);
+//   s = 1:  X[0][r] = G[0][r] + conj(V0) G[1][r],   X~[1][r] = conj(V2) G[0][r] + conj(V1) G[1][r],
+//           E~[p][0] = X[p][0] + X[p][1] W0,        E~[p][1] = X[p][0] W2 + X[p][1] W1,
+//           and since row 1 of X and column 1 of conj(b_01) carry a minus sign,
+//           E'_1[p][pp] = (-1)^{p+pp} E~[p][pp].
+// That is 33 complex MACs per site (chi^3/2 + chi^2/2 + 1 = 41 in the block
+// form).  The last site keeps its right bond open, so amp = sum of all entries.
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 zfma(double2 a, double2 b, double2 c) {  // a b + c
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zneg(double2 a) { return make_double2(-a.x, -a.y); }
+
+template <>
+struct Engine<4, QSVM_FP64> {
+  static constexpr int kRenormEvery = 8;
+  using Rec = Record<4, QSVM_FP64>;
+  double2 E[2][2][2];
+  int L;
+
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) E[c][q][r] = make_double2(0.0, 0.0);
+    E[0][0][0].x = 1.0;
+    L = 0;
+  }
+
+  __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
+    const double2* a = reinterpret_cast<const double2*>(sptr(ra));
+    const double2* b = reinterpret_cast<const double2*>(sptr(rb));
+    const double2 V0 = a[0], V1 = a[1], V2 = a[2], W0 = b[0], W1 = b[1], W2 = b[2];
+    const double2 r0 = make_double2(fma(V0.x, W0.x, V0.y * W0.y), fma(V0.x, W0.y, -V0.y * W0.x));  // conj(V0) W0
+    // G_0 = T + Im(rho_0) i E_1 and G_1 = T - Im(rho_0) i E_1 with T = E_0 + Re(rho_0) E_1
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const double2 e0 = E[0][q][r], e1 = E[1][q][r];
+        const double tr = fma(r0.x, e1.x, e0.x), ti = fma(r0.x, e1.y, e0.y);
+        E[0][q][r] = make_double2(fma(-r0.y, e1.y, tr), fma(r0.y, e1.x, ti));
+        E[1][q][r] = make_double2(fma(r0.y, e1.y, tr), fma(-r0.y, e1.x, ti));
+      }
+    double2 X[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      X[0][r] = zfma(V1, E[0][1][r], zmul(V2, E[0][0][r]));
+      X[1][r] = zfma(V0, E[0][1][r], E[0][0][r]);
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      E[0][p][0] = zfma(X[p][1], zconj(W1), zmul(X[p][0], zconj(W2)));
+      E[0][p][1] = zfma(X[p][1], zconj(W0), X[p][0]);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      X[0][r] = zfma(zconj(V0), E[1][1][r], E[1][0][r]);
+      X[1][r] = zfma(zconj(V1), E[1][1][r], zmul(zconj(V2), E[1][0][r]));  // X~[1][r]
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const double2 n0 = zfma(X[p][1], W0, X[p][0]);
+      const double2 n1 = zfma(X[p][1], W1, zmul(X[p][0], W2));
+      E[1][p][0] = p ? zneg(n0) : n0;
+      E[1][p][1] = p ? n1 : zneg(n1);
+    }
+    L -= 2;
+  }
+
+  __device__ __forceinline__ void renorm() {
+    double m = 0.0;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) m = fmax(m, fmax(fabs(E[s][p][r].x), fabs(E[s][p][r].y)));
+    if (!(m > 0.0) || !isfinite(m)) return;
+    int e;
+    frexp(m, &e);
+    if (e < -1000) e = -1000;
+    const double sc = ldexp(1.0, -e);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          E[s][p][r].x *= sc;
+          E[s][p][r].y *= sc;
+        }
+    L += e;
+  }
+
+  __device__ __forceinline__ void amplitude(double& re, double& im) const {
+    re = 0.0;
+    im = 0.0;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          re = __dadd_rn(re, E[s][p][r].x);
+          im = __dadd_rn(im, E[s][p][r].y);
+        }
+  }
+};
+
+// Form pair (V, iV) (f = 0) or (conj V, i conj V) (f = 1) of phase v of a record.
+template <int PREC>
+__device__ __forceinline__ void phase_form(uint32_t rec, int v, int f, int part, float2& x, float2& ix) {
+  const float4 q = *reinterpret_cast<const float4*>(sptr(rec + Record<4, PREC>::off(v, f, part)));
+  x = make_float2(q.x, q.y);
+  ix = make_float2(q.z, q.w);
+}
+// w V + acc, for w broadcast and V given by its form pair
+__device__ __forceinline__ float2 cmac(float2 w, float2 x, float2 ix, float2 acc) {
+  return fma2(bc(w.y), ix, fma2(bc(w.x), x, acc));
+}
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <>
+struct Engine<4, QSVM_FP32> {
+  static constexpr int kRenormEvery = 4;
+  using Rec = Record<4, QSVM_FP32>;
+  float2 E[2][2][2];
+  int L;
+
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) E[c][q][r] = make_float2(0.f, 0.f);
+    E[0][0][0].x = 1.f;
+    L = 0;
+  }
+
+  __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
+    const float2 z = make_float2(0.f, 0.f);
+    float2 x0, ix0, x1, ix1, x2, ix2;
+    // rho_0 = W0 conj(V0)
+    phase_form<QSVM_FP32>(rb, 0, 0, 0, x0, ix0);
+    phase_form<QSVM_FP32>(ra, 0, 1, 0, x1, ix1);
+    const float2 r0 = cmac(x0, x1, ix1, z);
+    const float2 R0 = r0, iR0 = make_float2(-r0.y, r0.x), R1 = make_float2(r0.x, -r0.y), iR1 = make_float2(r0.y, r0.x);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const float2 e0 = E[0][q][r], e1 = E[1][q][r];
+        E[0][q][r] = cmac(e1, R0, iR0, e0);
+        E[1][q][r] = cmac(e1, R1, iR1, e0);
+      }
+    float2 X[2][2];
+    // s = 0: row phases in a-form, column phases in b-form
+    phase_form<QSVM_FP32>(ra, 0, 0, 0, x0, ix0);
+    phase_form<QSVM_FP32>(ra, 1, 0, 0, x1, ix1);
+    phase_form<QSVM_FP32>(ra, 2, 0, 0, x2, ix2);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      X[0][r] = cmac(E[0][1][r], x1, ix1, cmac(E[0][0][r], x2, ix2, z));
+      X[1][r] = cmac(E[0][1][r], x0, ix0, E[0][0][r]);
+    }
+    phase_form<QSVM_FP32>(rb, 0, 1, 0, x0, ix0);
+    phase_form<QSVM_FP32>(rb, 1, 1, 0, x1, ix1);
+    phase_form<QSVM_FP32>(rb, 2, 1, 0, x2, ix2);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      E[0][p][0] = cmac(X[p][1], x1, ix1, cmac(X[p][0], x2, ix2, z));
+      E[0][p][1] = cmac(X[p][1], x0, ix0, X[p][0]);
+    }
+    // s = 1: row phases in b-form, column phases in a-form
+    phase_form<QSVM_FP32>(ra, 0, 1, 0, x0, ix0);
+    phase_form<QSVM_FP32>(ra, 1, 1, 0, x1, ix1);
+    phase_form<QSVM_FP32>(ra, 2, 1, 0, x2, ix2);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      X[0][r] = cmac(E[1][1][r], x0, ix0, E[1][0][r]);
+      X[1][r] = cmac(E[1][1][r], x1, ix1, cmac(E[1][0][r], x2, ix2, z));  // X~[1][r]
+    }
+    phase_form<QSVM_FP32>(rb, 0, 0, 0, x0, ix0);
+    phase_form<QSVM_FP32>(rb, 1, 0, 0, x1, ix1);
+    phase_form<QSVM_FP32>(rb, 2, 0, 0, x2, ix2);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const float2 n0 = cmac(X[p][1], x0, ix0, X[p][0]);
+      const float2 n1 = cmac(X[p][1], x1, ix1, cmac(X[p][0], x2, ix2, z));
+      E[1][p][0] = p ? neg2(n0) : n0;
+      E[1][p][1] = p ? n1 : neg2(n1);
+    }
+    L -= 2;
+  }
+
+  __device__ __forceinline__ void renorm() {
+    const float m = max_abs<8>(reinterpret_cast<const float2(&)[8]>(E));
+    if (!(m > 0.f) || !isfinite(m)) return;
+    int e = exp_of(m);
+    if (e < -120) {  // subnormal territory: scale in two exact steps
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int r = 0; r < 2; ++r) E[s][p][r] = mul2(E[s][p][r], bc(pow2f(100)));
+      L -= 100;
+      e += 100;
+    }
+    const float2 sc = bc(pow2f(-e));
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) E[s][p][r] = mul2(E[s][p][r], sc);
+    L += e;
+  }
+
+  __device__ __forceinline__ void amplitude(double& re, double& im) const {
+    re = 0.0;
+    im = 0.0;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          re = __dadd_rn(re, (double)E[s][p][r].x);
+          im = __dadd_rn(im, (double)E[s][p][r].y);
+        }
+  }
+};
+
+// Split FP32 in phase form.  Grids as in the block form except that the phases
+// have modulus 1 instead of 1/2, which the two intermediate grids absorb: G on
+// 2^-9 (|G| <= 1 + sqrt(2); X = V G sums 4 products <= 4 * 2^11 * 1236.5 < 1.02e7
+// units of 2^-20) and X on 2^-8 (|X| <= 4 sqrt(2); E' sums 4 products
+// <= 4 * 2^11 * 1448.7 < 1.19e7 units of 2^-19); the identity entries add an
+// operand already on the coarser grid.  Both stay below 2^24 = 1.68e7.
+struct SplitForm {
+  float2 h, ih, l, il;
+};
+
+template <>
+struct Engine<4, QSVM_FP32_SPLIT> {
+  static constexpr int GG = 9, GX = 8;
+  static constexpr int kRenormEvery = 1;  // built into site()
+  using Rec = Record<4, QSVM_FP32_SPLIT>;
+  float2 Eh[2][2][2], El[2][2][2], Ef[2][2][2];  // Ef = fl(Eh + El)
+  int L;
+
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) Eh[c][q][r] = El[c][q][r] = Ef[c][q][r] = make_float2(0.f, 0.f);
+    Eh[0][0][0].x = Ef[0][0][0].x = 1.f;
+    L = 0;
+  }
+
+  static __device__ __forceinline__ SplitForm form(uint32_t rec, int v, int f) {
+    SplitForm F;
+    phase_form<QSVM_FP32_SPLIT>(rec, v, f, 0, F.h, F.ih);
+    phase_form<QSVM_FP32_SPLIT>(rec, v, f, 1, F.l, F.il);
+    return F;
+  }
+  // (hh, ll) += w V for a split w (hi, lo, full) and a split form of V
+  static __device__ __forceinline__ void smac(float2& hh, float2& ll, float2 wh, float2 wl, float2 wf,
+                                              const SplitForm& V) {
+    hh = fma2(bc(wh.x), V.h, hh);
+    hh = fma2(bc(wh.y), V.ih, hh);
+    ll = fma2(bc(wl.x), V.h, ll);
+    ll = fma2(bc(wl.y), V.ih, ll);
+    ll = fma2(bc(wf.x), V.l, ll);
+    ll = fma2(bc(wf.y), V.il, ll);
+  }
+  template <int GR>
+  static __device__ __forceinline__ void ssplit(float2 hh, float2 ll, float2& xh, float2& xl, float2& xf) {
+    const float2 v = add2(hh, ll);
+    xh = grid_round2<GR>(v);
+    xl = add2(fma2(xh, make_float2(-1.f, -1.f), hh), ll);  // (hh - xh) is exact
+    xf = v;
+  }
+
+  __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
+    const float2 z = make_float2(0.f, 0.f);
+    float2 Rh[2], iRh[2], Rl[2], iRl[2];
+    // rho_0 = W0 conj(V0): W0's a-form entries and V0's b-form entries
+    split_phase(rb + Rec::off(0, 0, 0), rb + Rec::off(0, 0, 1), ra + Rec::off(0, 1, 0), ra + Rec::off(0, 1, 1), Rh, iRh,
+                Rl, iRl);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const float2 e0h = Eh[0][q][r], e0l = El[0][q][r];
+        const float2 e1h = Eh[1][q][r], e1l = El[1][q][r], e1f = Ef[1][q][r];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          split_mix<GG>(e0h, e0l, e1h, e1l, e1f, Rh[s], iRh[s], Rl[s], iRl[s], Eh[s][q][r], El[s][q][r],
+                        Ef[s][q][r]);
+      }
+    float2 Nh[2][2][2], Nl[2][2][2];
+    float2 Xh[2][2], Xl[2][2], Xf[2][2];
+    {  // s = 0
+      const SplitForm V0 = form(ra, 0, 0), V1 = form(ra, 1, 0), V2 = form(ra, 2, 0);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float2 hh = z, ll = z;
+        smac(hh, ll, Eh[0][0][r], El[0][0][r], Ef[0][0][r], V2);
+        smac(hh, ll, Eh[0][1][r], El[0][1][r], Ef[0][1][r], V1);
+        ssplit<GX>(hh, ll, Xh[0][r], Xl[0][r], Xf[0][r]);
+        hh = Eh[0][0][r];
+        ll = El[0][0][r];
+        smac(hh, ll, Eh[0][1][r], El[0][1][r], Ef[0][1][r], V0);
+        ssplit<GX>(hh, ll, Xh[1][r], Xl[1][r], Xf[1][r]);
+      }
+      const SplitForm W0 = form(rb, 0, 1), W1 = form(rb, 1, 1), W2 = form(rb, 2, 1);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 hh = z, ll = z;
+        smac(hh, ll, Xh[p][0], Xl[p][0], Xf[p][0], W2);
+        smac(hh, ll, Xh[p][1], Xl[p][1], Xf[p][1], W1);
+        Nh[0][p][0] = hh;
+        Nl[0][p][0] = ll;
+        hh = Xh[p][0];
+        ll = Xl[p][0];
+        smac(hh, ll, Xh[p][1], Xl[p][1], Xf[p][1], W0);
+        Nh[0][p][1] = hh;
+        Nl[0][p][1] = ll;
+      }
+    }
+    {  // s = 1 (row 1 of X holds X~; the signs are applied below)
+      const SplitForm V0 = form(ra, 0, 1), V1 = form(ra, 1, 1), V2 = form(ra, 2, 1);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float2 hh = Eh[1][0][r], ll = El[1][0][r];
+        smac(hh, ll, Eh[1][1][r], El[1][1][r], Ef[1][1][r], V0);
+        ssplit<GX>(hh, ll, Xh[0][r], Xl[0][r], Xf[0][r]);
+        hh = z;
+        ll = z;
+        smac(hh, ll, Eh[1][0][r], El[1][0][r], Ef[1][0][r], V2);
+        smac(hh, ll, Eh[1][1][r], El[1][1][r], Ef[1][1][r], V1);
+        ssplit<GX>(hh, ll, Xh[1][r], Xl[1][r], Xf[1][r]);
+      }
+      const SplitForm W0 = form(rb, 0, 0), W1 = form(rb, 1, 0), W2 = form(rb, 2, 0);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 hh = Xh[p][0], ll = Xl[p][0];
+        smac(hh, ll, Xh[p][1], Xl[p][1], Xf[p][1], W0);
+        Nh[1][p][0] = hh;
+        Nl[1][p][0] = ll;
+        hh = z;
+        ll = z;
+        smac(hh, ll, Xh[p][0], Xl[p][0], Xf[p][0], W2);
+        smac(hh, ll, Xh[p][1], Xl[p][1], Xf[p][1], W1);
+        Nh[1][p][1] = hh;
+        Nl[1][p][1] = ll;
+      }
+    }
+    // renormalise by 2^-e, apply the signs (-1)^{p+pp} of block 1, re-split onto the E grid
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 V[2][2][2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) V[s][p][r] = add2(Nh[s][p][r], Nl[s][p][r]);
+    const float m = max_abs<8>(reinterpret_cast<const float2(&)[8]>(V));
+    int e = 0;
+    if (m > 0.f && isfinite(m)) {
+      e = exp_of(m);
+      if (e < -120) {  // collapse to near zero: scale up in two exact steps
+        const float2 up = bc(pow2f(100));
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+          for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              Nh[s][p][r] = mul2(Nh[s][p][r], up);
+              Nl[s][p][r] = mul2(Nl[s][p][r], up);
+              V[s][p][r] = mul2(V[s][p][r], up);
+            }
+        L -= 100;
+        e += 100;
+      }
+    }
+    const float sc = pow2f(-e);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const float2 scs = bc((s == 1 && ((p + r) & 1)) ? -sc : sc);
+          const float2 f = mul2(V[s][p][r], scs);
+          const float2 h = grid_round2<kGridE>(f);
+          Eh[s][p][r] = h;
+          El[s][p][r] = fma2(Nl[s][p][r], scs, fma2(h, m1, mul2(Nh[s][p][r], scs)));
+          Ef[s][p][r] = f;
+        }
+    L += e - 2;
+  }
+
+  __device__ __forceinline__ void renorm() {}
+
+  __device__ __forceinline__ void amplitude(double& re, double& im) const {
+    re = 0.0;
+    im = 0.0;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          re = __dadd_rn(re, __dadd_rn((double)Eh[s][p][r].x, (double)El[s][p][r].x));
+          im = __dadd_rn(im, __dadd_rn((double)Eh[s][p][r].y, (double)El[s][p][r].y));
+        }
   }
 };
 
@@ -556,7 +1003,8 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     const float2 m1 = make_float2(-1.f, -1.f);
     float2 Rh[2], iRh[2], Rl[2], iRl[2];
-    split_phase(ra + Rec::kPhaseOff, rb + Rec::kPhaseOff, Rh, iRh, Rl, iRl);
+    split_phase(ra + Rec::kPhaseOff, ra + Rec::kPhaseOff + 16, rb + Rec::kPhaseOff, rb + Rec::kPhaseOff + 16, Rh, iRh,
+                Rl, iRl);
     const float2 rh = s ? Rh[1] : Rh[0], irh = s ? iRh[1] : iRh[0];
     const float2 rl = s ? Rl[1] : Rl[0], irl = s ? iRl[1] : iRl[0];
     // own rows of G_s from the same rows of E_0 and E_1
@@ -699,8 +1147,8 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
   __device__ __forceinline__ void amplitude(double& re, double& im) const {
     const float4 a = *entry(0, 0, 0);
     const float4 b = *entry(1, 0, 0);
-    re = ((double)a.x + (double)a.z) + ((double)b.x + (double)b.z);
-    im = ((double)a.y + (double)a.w) + ((double)b.y + (double)b.w);
+    re = __dadd_rn(__dadd_rn((double)a.x, (double)a.z), __dadd_rn((double)b.x, (double)b.z));
+    im = __dadd_rn(__dadd_rn((double)a.y, (double)a.w), __dadd_rn((double)b.y, (double)b.w));
   }
 };
 
@@ -900,10 +1348,11 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
     if (Eng::kRenormEvery > 1) eng.renorm();
     double re, im;
     eng.amplitude(re, im);
-    const double a2 = re * re + im * im;
+    // explicit roundings, so every kernel that runs this epilogue gives the same bits
+    const double a2 = __fma_rn(re, re, __dmul_rn(im, im));
     if (a2 > 0.0) {
       kval = ldexp(a2, 2 * eng.L);
-      lval = log(a2) + (double)(2 * eng.L) * 0.69314718055994530942;
+      lval = __fma_rn((double)(2 * eng.L), 0.69314718055994530942, log(a2));
     }
     w.K[(i0 + ty) * w.ldk + (j0 + tx)] = kval;
     if (w.logK) w.logK[(i0 + ty) * w.ldl + (j0 + tx)] = lval;

@@ -72,7 +72,7 @@ int64_t tiles_per_side(int64_t n_points, int tdim) { return (n_points + tdim - 1
 
 // byte offset of the column-side (b-form) records inside an MPS buffer
 size_t form_b_offset(int64_t n_points, int n_qubits, int reps, int prec) {
-  return record_forms(prec) == 2 ? record_bytes(1 << reps, prec) * (size_t)n_points * (size_t)n_qubits : 0;
+  return record_forms(1 << reps, prec) == 2 ? record_bytes(1 << reps, prec) * (size_t)n_points * (size_t)n_qubits : 0;
 }
 
 // selected pipeline configuration per (reps - 1, precision); -1 = default
@@ -210,7 +210,7 @@ size_t qsvm_mps_record_bytes(int32_t reps, int32_t precision) {
 
 size_t qsvm_mps_bytes(int32_t n_qubits, int32_t reps, int64_t n_points, int32_t precision) {
   if (n_qubits < 1 || n_points < 0) return 0;
-  return qsvm_mps_record_bytes(reps, precision) * (size_t)record_forms(precision) * (size_t)n_qubits *
+  return qsvm_mps_record_bytes(reps, precision) * (size_t)record_forms(1 << reps, precision) * (size_t)n_qubits *
          (size_t)n_points;
 }
 

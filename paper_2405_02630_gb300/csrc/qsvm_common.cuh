@@ -1,8 +1,9 @@
 // qsvm_common.cuh -- device-side helpers shared by the libqsvm kernels.
 //
-// Site-record layout (see include/qsvm.h): the two chi/2 x chi/2 blocks
-// a_0s[q][p] = A[s][2q][2p+s] (s = 0, 1), then the phase r = e^{2 i theta_k}
-// that gives the other two, a_1s = r_s a_0s with r_0 = r and r_1 = conj(r).
+// Site-record layouts (see include/qsvm.h): reps = 1, 3 store the two chi/2 x
+// chi/2 blocks a_0s[q][p] = A[s][2q][2p+s] (s = 0, 1), then the phase
+// r = e^{2 i theta_k} that gives the other two, a_1s = r_s a_0s with r_0 = r and
+// r_1 = conj(r); reps = 2 stores three unit phases that determine the site.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,11 +26,11 @@ constexpr int kGridE = 10;
 constexpr int kGridG = 10;
 __host__ __device__ constexpr int grid_x(int chi) { return chi >= 8 ? 9 : 10; }
 
-// Site-record geometry.  A record holds the blocks a_00 and a_01 (16 bytes per
-// complex entry) and then the phase entry r.  FP64 records hold each value once as
-// (re, im).  The FP32 formats hold two forms of every record, in two arrays (all
-// row-side "a-form" records of the buffer first, then all column-side "b-form"
-// records):
+// Site-record geometry, block form (reps = 1 and 3).  A record holds the blocks
+// a_00 and a_01 (16 bytes per complex entry) and then the phase entry r.  FP64
+// records hold each value once as (re, im).  The FP32 formats hold two forms of
+// every record, in two arrays (all row-side "a-form" records of the buffer first,
+// then all column-side "b-form" records):
 //   a-form entry (A, iA)              = (re, im, -im, re)
 //   b-form entry (conj B, i conj B)   = (re, -im, im, re)
 // so that a complex multiply-accumulate is two packed FP32x2 FMAs with one
@@ -53,18 +54,41 @@ struct Record {
   static constexpr int kBytes = kPhaseOff + kParts * kEntryBytes;  // one form of one site
 };
 
+// Phase form (reps = 2).  With P = e^{-i x_k} and T = e^{-i theta_{k-1}}, the
+// site's blocks are a_00 = (1/2) [[P^2 T^2, 1], [P^2, T^2]] and
+// a_01 = (1/2) [[1, -conj(P^2 T^2)], [conj(T^2), -conj(P^2)]] (rows q, columns p),
+// and r = conj(T^2).  A record holds the three unit phases V_0 = T^2, V_1 = P^2,
+// V_2 = P^2 T^2 (the factors 1/2 are carried in the log scale).  FP64: (re, im)
+// doubles.  FP32: per value its a-form then its b-form entry (each side of a
+// pair needs both), one array.  Split FP32: the hi entries of the three values
+// (both forms), then the lo entries.
+template <int PREC>
+struct Record<4, PREC> {
+  static constexpr int H = 2;
+  static constexpr int kForms = 1;
+  static constexpr int kParts = (PREC == QSVM_FP32_SPLIT) ? 2 : 1;
+  static constexpr int kValBytes = (PREC == QSVM_FP64) ? 16 : 32;  // one value, all its forms, one part
+  static constexpr int kPartBytes = 3 * kValBytes;
+  static constexpr int kBytes = kParts * kPartBytes;
+  // byte offset of value v (0: T^2, 1: P^2, 2: P^2 T^2), form f (0: a, 1: b), part (0: hi, 1: lo)
+  __host__ __device__ static constexpr int off(int v, int f, int part) { return part * kPartBytes + v * kValBytes + f * 16; }
+};
+
 __host__ __device__ constexpr size_t record_bytes(int chi, int prec) {
-  return (2 * (size_t)(chi / 2) * (chi / 2) + 1) * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1) +
-         ((chi >= 8 && prec == QSVM_FP32_SPLIT) ? 32 : 0);
+  return chi == 4 ? (prec == QSVM_FP64 ? 48 : prec == QSVM_FP32 ? 96 : 192)
+                  : (2 * (size_t)(chi / 2) * (chi / 2) + 1) * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1) +
+                        ((chi >= 8 && prec == QSVM_FP32_SPLIT) ? 32 : 0);
 }
 static_assert(record_bytes(4, QSVM_FP64) == Record<4, QSVM_FP64>::kBytes, "record geometry");
+static_assert(record_bytes(4, QSVM_FP32) == Record<4, QSVM_FP32>::kBytes, "record geometry");
+static_assert(record_bytes(4, QSVM_FP32_SPLIT) == Record<4, QSVM_FP32_SPLIT>::kBytes, "record geometry");
 static_assert(record_bytes(2, QSVM_FP32) == Record<2, QSVM_FP32>::kBytes, "record geometry");
 static_assert(record_bytes(8, QSVM_FP32_SPLIT) == Record<8, QSVM_FP32_SPLIT>::kBytes, "record geometry");
-static_assert(record_bytes(4, QSVM_FP32_SPLIT) == Record<4, QSVM_FP32_SPLIT>::kBytes, "record geometry");
 static_assert(record_bytes(8, QSVM_FP64) == Record<8, QSVM_FP64>::kBytes, "record geometry");
-static_assert(Record<4, QSVM_FP32_SPLIT>::kBytes % 16 == 0 && Record<2, QSVM_FP64>::kBytes % 16 == 0,
+static_assert(Record<2, QSVM_FP32_SPLIT>::kBytes % 16 == 0 && Record<2, QSVM_FP64>::kBytes % 16 == 0,
               "bulk copies move whole 16-byte units");
-inline int record_forms(int prec) { return prec == QSVM_FP64 ? 1 : 2; }
+// arrays of records a buffer holds (the FP32 block forms keep a- and b-form arrays)
+__host__ __device__ constexpr int record_forms(int chi, int prec) { return (prec == QSVM_FP64 || chi == 4) ? 1 : 2; }
 
 // ---- tile order --------------------------------------------------------------
 // Pair tiles are visited in bands of kBandRows tile rows; within a band column by

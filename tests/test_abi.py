@@ -18,17 +18,22 @@ def test_exports_every_declared_symbol():
 
 
 def test_record_and_mps_bytes():
-    # per site the blocks a_00, a_01 (chi^2 / 2 complex entries) and the phase r, 16 bytes
-    # each; split FP32 holds hi and lo; FP32 formats hold two forms
-    for reps, chi in ((1, 2), (2, 4), (3, 8)):
+    # block form (reps 1, 3): per site the blocks a_00, a_01 (chi^2 / 2 complex entries) and
+    # the phase r, 16 bytes each; split FP32 holds hi and lo; FP32 formats hold two forms
+    for reps, chi in ((1, 2), (3, 8)):
         entries = 2 * (chi // 2) ** 2 + 1  # blocks a_00, a_01 and the phase r
         assert qsvm.qsvm_mps_record_bytes(reps, "fp64") == entries * 16
         assert qsvm.qsvm_mps_record_bytes(reps, "fp32") == entries * 16
         pad = 32 if chi == 8 else 0  # 16 bytes after each block of the four-thread layout
         assert qsvm.qsvm_mps_record_bytes(reps, "fp32_split") == entries * 32 + pad
-    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp64") == 8192 * 784 * 144
-    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32") == 2 * 8192 * 784 * 144
-    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 2 * 8192 * 784 * 288
+    assert qsvm.qsvm_mps_bytes(64, 3, 10, "fp32") == 2 * 10 * 64 * 33 * 16
+    # reps = 2, phase form: three phases, (re, im) doubles or both forms of 16 bytes, hi and lo
+    assert qsvm.qsvm_mps_record_bytes(2, "fp64") == 48
+    assert qsvm.qsvm_mps_record_bytes(2, "fp32") == 96
+    assert qsvm.qsvm_mps_record_bytes(2, "fp32_split") == 192
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp64") == 8192 * 784 * 48
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32") == 8192 * 784 * 96
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 8192 * 784 * 192
     assert qsvm.qsvm_mps_record_bytes(4, "fp64") == 0
     assert qsvm.qsvm_mps_record_bytes(2, 7) == 0
 
@@ -135,7 +140,7 @@ def test_configs():
                 S, st = qsvm.qsvm_config_info(c, reps, prec)
                 assert S >= 1 and 2 <= st <= 4
     S2, _ = qsvm.qsvm_config_info(1, 2, "fp32_split")
-    assert S2 == 3  # 1 KB of 288-byte records per point and chunk
+    assert S2 == 5  # 1 KB of 192-byte records per point and chunk
     assert qsvm.qsvm_get_config(2, "fp64") == -1
     qsvm.qsvm_set_config(2, "fp64", 0)
     assert qsvm.qsvm_get_config(2, "fp64") == 0

@@ -33,21 +33,31 @@ def _dev(X):
 
 
 def _decode_fp64(buf, N, n, reps):
-    """Site tensors A[i, k, sigma, t, u] from FP64 records (layout of include/qsvm.h):
-    blocks a_0s[q][p] = A[s][2q][2p+s], then r; the rows with c = 1 are a_1s = r_s a_0s
-    with r_0 = r, r_1 = conj(r)."""
+    """Site tensors A[i, k, sigma, t, u] from FP64 records (layouts of include/qsvm.h).
+    Block form (reps 1, 3): a_0s[q][p] = A[s][2q][2p+s], then r; the rows with c = 1 are
+    a_1s = r_s a_0s with r_0 = r, r_1 = conj(r).  Phase form (reps 2): V0 = T^2, V1 = P^2,
+    V2 = P^2 T^2 give a_00 = [[V2, 1], [V1, V0]] / 2, a_01 = [[1, -conj V2], [conj V0, -conj V1]] / 2
+    and r = conj(V0); the last site's right bond is left open."""
     chi = 2 ** reps
     H = chi // 2
-    raw = buf.cpu().numpy().view(np.complex128).reshape(N, n, 2 * H * H + 1)
-    r = raw[:, :, 2 * H * H]
     A = np.zeros((N, n, 2, chi, chi), complex)
+    if reps == 2:
+        raw = buf.cpu().numpy().view(np.complex128).reshape(N, n, 3)
+        V0, V1, V2 = raw[..., 0], raw[..., 1], raw[..., 2]
+        one = np.ones_like(V0)
+        blocks = [np.stack([np.stack([V2, one], -1), np.stack([V1, V0], -1)], -2) / 2,
+                  np.stack([np.stack([one, -np.conj(V2)], -1), np.stack([np.conj(V0), -np.conj(V1)], -1)], -2) / 2]
+        r = np.conj(V0)
+    else:
+        raw = buf.cpu().numpy().view(np.complex128).reshape(N, n, 2 * H * H + 1)
+        blocks = [raw[:, :, s * H * H:(s + 1) * H * H].reshape(N, n, H, H) for s in range(2)]
+        r = raw[:, :, 2 * H * H]
     for s in range(2):
-        a0 = raw[:, :, s * H * H:(s + 1) * H * H].reshape(N, n, H, H)
         rs = r if s == 0 else np.conj(r)
         for qq in range(H):
             for p in range(H):
-                A[:, :, s, 2 * qq, 2 * p + s] = a0[:, :, qq, p]
-                A[:, :, s, 2 * qq + 1, 2 * p + s] = rs * a0[:, :, qq, p]
+                A[:, :, s, 2 * qq, 2 * p + s] = blocks[s][:, :, qq, p]
+                A[:, :, s, 2 * qq + 1, 2 * p + s] = rs * blocks[s][:, :, qq, p]
     return A
 
 
@@ -93,10 +103,14 @@ def test_build_mps_lowprec_formats(q):
     N, n, reps = 5, 33, 2
     X = inputs.mnist_like_features(N, n, 77)
     d = _dev(X)
-    E = 9  # entries per record: two 2 x 2 blocks and the phase
-    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, E)
-    f32 = q.qsvm_build_mps(d, reps, "fp32").cpu().numpy().view(np.float32).reshape(2, N * n, E, 4)
-    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(2, N * n, 2 * E, 4)
+    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, 3)
+    f32 = q.qsvm_build_mps(d, reps, "fp32").cpu().numpy().view(np.float32).reshape(N * n, 3, 2, 4)
+    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(N * n, 2, 3, 2, 4)
+    # the phases T^2, P^2, P^2 T^2 with theta_{k-1} = (pi - x_{k-1})(pi - x_k) (0 at site 0)
+    theta = np.concatenate([np.zeros((N, 1)), (np.pi - X[:, :-1]) * (np.pi - X[:, 1:])], axis=1).reshape(-1)
+    x = X.reshape(-1)
+    want = np.stack([np.exp(-2j * theta), np.exp(-2j * x), np.exp(-2j * (x + theta))], axis=1)
+    assert np.max(np.abs(f64 - want)) <= 1e-14
 
     def check_forms(a, b):  # a-form (re, im, -im, re); b-form (re, -im, im, re)
         re, im = a[..., 0], a[..., 1]
@@ -105,23 +119,37 @@ def test_build_mps_lowprec_formats(q):
         assert np.array_equal(b[..., 2], im) and np.array_equal(b[..., 3], re)
         return re.astype(np.float64) + 1j * im.astype(np.float64)
 
-    v32 = check_forms(f32[0], f32[1])
-    # FP32 records are the FP64 values rounded to float (within half an ulp, plus
-    # slack for the 1e-17 noise the two builds may carry in entries that are 0)
+    v32 = check_forms(f32[..., 0, :], f32[..., 1, :])
     for a, b in ((v32.real, f64.real), (v32.imag, f64.imag)):
         assert np.all(np.abs(a - b) <= np.abs(b) * 2.0 ** -24 + 1e-15)
-    # split: per block 4 hi entries then 4 lo entries; then the phase's hi and lo entry
-    hi_idx = [0, 1, 2, 3, 8, 9, 10, 11, 16]
-    lo_idx = [4, 5, 6, 7, 12, 13, 14, 15, 17]
-    hi = check_forms(spl[0][:, hi_idx], spl[1][:, hi_idx])
-    lo = check_forms(spl[0][:, lo_idx], spl[1][:, lo_idx])
+    hi = check_forms(spl[:, 0, :, 0, :], spl[:, 0, :, 1, :])
+    lo = check_forms(spl[:, 1, :, 0, :], spl[:, 1, :, 1, :])
     for part in (hi.real, hi.imag):
         assert np.array_equal(np.round(part * 2048) / 2048, part)
     assert np.max(np.abs(hi + lo - f64)) <= 2 ** -34
-    # the phase entry is exp(2 i theta_{k-1}) (1 at site 0)
-    theta = (np.pi - X[:, :-1]) * (np.pi - X[:, 1:])
-    r = np.concatenate([np.ones((N, 1)), np.exp(2j * theta)], axis=1).reshape(-1)
-    assert np.max(np.abs(f64[:, 8] - r)) <= 1e-14
+
+
+def test_build_mps_block_formats_reps3(q):
+    """Block-form records (reps = 3): FP64 (re, im) entries; split hi on the 2^-11 grid,
+    hi + lo within 2^-34 of FP64; the phase entry is exp(2 i theta_{k-1})."""
+    N, n, reps = 3, 9, 3
+    X = inputs.uniform_features(N, n, 91)
+    d = _dev(X)
+    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, 33)
+    theta = np.concatenate([np.zeros((N, 1)), (np.pi - X[:, :-1]) * (np.pi - X[:, 1:])], axis=1).reshape(-1)
+    assert np.max(np.abs(f64[:, 32] - np.exp(2j * theta))) <= 1e-14
+    rec = q.qsvm_mps_record_bytes(reps, "fp32_split") // 4  # floats per a-form record
+    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(2, N * n, rec)
+    a = spl[0]
+    # 16-byte entries: block s starts at entry 33 s (16 hi entries, 16 lo, one unused), the phase at entry 66
+    for s in range(2):
+        for e in range(16):
+            h = a[:, 4 * (s * 33 + e):4 * (s * 33 + e) + 2]
+            lo = a[:, 4 * (s * 33 + 16 + e):4 * (s * 33 + 16 + e) + 2]
+            assert np.array_equal(np.round(h * 2048) / 2048, h)
+            h64, lo64 = h.astype(np.float64), lo.astype(np.float64)
+            v = (h64[:, 0] + lo64[:, 0]) + 1j * (h64[:, 1] + lo64[:, 1])
+            assert np.max(np.abs(v - f64[:, s * 16 + e])) <= 2 ** -30
 
 
 # ----------------------------------------------------------- small Grams ---
