@@ -52,10 +52,14 @@ def structured_cmacs_per_entry(n: int, reps: int) -> int:
 
 
 def factorized_cmacs_per_entry(n: int, reps: int) -> int:
-    """Complex MACs per kernel entry of the contraction as the kernels carry it out:
-    per site rho = r(i) conj(r(j)) (1), G_s = E_0 + rho_s E_1 (chi^2/2),
-    X_s = a_0s^T G_s and E'_s = X_s conj(b_0s) (chi^3/4 each), bonds padded to chi."""
+    """Complex MACs per kernel entry of the contraction as the kernels carry it out.
+    Block form (reps 1, 3): per site rho = r(i) conj(r(j)) (1), G_s = E_0 + rho_s E_1
+    (chi^2/2), X_s = a_0s^T G_s and E'_s = X_s conj(b_0s) (chi^3/4 each), bonds padded to chi.
+    Phase form (reps 2): rho (1), G (8), X and E' with the unit entries of a and b added
+    rather than multiplied (12 each): 33."""
     chi = 2 ** reps
+    if reps == 2:
+        return n * 33
     return n * (chi ** 3 // 2 + chi ** 2 // 2 + 1)
 
 
@@ -71,7 +75,7 @@ FMA_PER_CMAC = {"fp32": 4, "fp32_split": 12, "fp64": 4}
 # same configuration with the default pipeline shape (dram__bytes_read.sum +
 # dram__bytes_write.sum; profiles/pair_tile_split_n784_r2.md).  Configurations
 # not captured with the current kernel report null.
-MEASURED_TRAFFIC_BYTES = {}
+MEASURED_TRAFFIC_BYTES = {("gram_n784_r2_N8192", "fp32_split"): 40_496_324_096 + 559_182_080}
 
 
 class ClockSampler:
