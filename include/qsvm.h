@@ -68,33 +68,43 @@ enum qsvm_precision {
 };
 
 /* ---- MPS storage ---------------------------------------------------------
- * The feature map ends with a diagonal layer, so the physical index of site k
- * equals the last-repetition spin carried on its right bond: with the right
- * bond index u = 2p + s and left bond index t = 2q + c, the tensor
- * A_k[sigma][t][u] is nonzero only when sigma == s.  The left bit c (the left
- * neighbour's last-repetition spin) enters only through the last repetition's
- * ZZ phase, so the blocks a_cs[q][p] = A_k[s][2q+c][2p+s] satisfy
- * a_1s = r_s a_0s with r_0 = exp(2 i theta_{k-1}) and r_1 = conj(r_0)
- * (theta_{k-1} = (pi - x_{k-1})(pi - x_k); r = 1 at site 0).  A site record
- * stores the two chi/2 x chi/2 blocks a_00, a_01, each row-major over (q, p),
- * then the phase r, 16 bytes per complex value:
+ * One record per (point, site), point-major: record (i, k) at byte
+ * (i * n_qubits + k) * qsvm_mps_record_bytes(reps, precision).  With
+ * P = exp(-i x_k), T = exp(-i theta_{k-1}), theta_{k-1} = (pi - x_{k-1})(pi - x_k)
+ * (T = 1 at site 0), z(b) = 1 - 2b, right bond index u = 2p + s and left bond
+ * index t = 2q + c, the site tensor is A_k[sigma][t][u] = 0 unless sigma == s
+ * (the last layer is diagonal), and its blocks a_cs[q][p] = A_k[s][2q+c][2p+s]
+ * satisfy a_1s = r_s a_0s with r_0 = conj(T^2) and r_1 = T^2.
+ *
+ * Phase form (reps = 2): every entry is +-1/2 times 1, T^2, P^2 or P^2 T^2 or a
+ * conjugate, a_00 = (1/2) [[P^2 T^2, 1], [P^2, T^2]] and
+ * a_01 = (1/2) [[1, -conj(P^2 T^2)], [conj(T^2), -conj(P^2)]] (rows q, columns p),
+ * and the record holds the three phases V0 = T^2, V1 = P^2, V2 = P^2 T^2:
+ *   QSVM_FP64        (re, im) doubles, 48 bytes;
+ *   QSVM_FP32        per value its a-form then its b-form entry (below), 96 bytes;
+ *   QSVM_FP32_SPLIT  the hi entries of the three values (re and im on the 2^-11
+ *                    grid, both forms), then the lo entries, 192 bytes.
+ * The last site's tensor keeps its right bond open (its layer-1 spin is summed
+ * by the contraction).  One array of records.
+ *
+ * Block form (reps = 1 and 3): the record stores the two chi/2 x chi/2 blocks
+ * a_00, a_01, each row-major over (q, p), then the phase r_0, 16 bytes per value:
  *   QSVM_FP64        (re, im) as two doubles;
- *   QSVM_FP32        one "form" entry of four floats (below);
+ *   QSVM_FP32        one "form" entry of four floats;
  *   QSVM_FP32_SPLIT  per block: the chi^2/4 "hi" form entries (re and im on the
  *                    2^-11 grid), then the chi^2/4 "lo" form entries; the phase
- *                    as a hi entry then a lo entry.
- * qsvm_mps_record_bytes() is the size of one record: (chi^2/2 + 1) x 16 bytes,
- * twice that for QSVM_FP32_SPLIT, where at reps = 3 each block is also followed
- * by 16 unused bytes (shared-memory bank spreading).  FP64 buffers hold one record per
- * (point, site), point-major: record (i, k) at byte
- * (i * n_qubits + k) * record_bytes.  The FP32 formats hold two forms of every
- * record in two consecutive arrays of that layout: first the row-side a-form,
- * entry (re, im, -im, re) = (A, iA); then the column-side b-form, entry
- * (re, -im, im, re) = (conj A, i conj A).  With them a complex multiply-add is
- * two packed FP32x2 FMAs.  Site 0 has a left bond of dimension 1 (only t = 0 is
- * nonzero); the last site has a right bond of dimension 2 holding the physical
- * index (u = sigma, p = 0).  The layout is private to this library: produce it
- * with qsvm_build_mps and size it with qsvm_mps_bytes. */
+ *                    as a hi entry then a lo entry; at reps = 3 each block is
+ *                    followed by 16 unused bytes (shared-memory bank spreading).
+ * Site 0 has a left bond of dimension 1 (only t = 0 is nonzero); the last site
+ * has a right bond of dimension 2 holding the physical index (u = sigma, p = 0).
+ * The FP32 block formats hold two arrays of records: first the row-side a-forms,
+ * then the column-side b-forms.
+ *
+ * Forms: an a-form entry of a complex value A is (re, im, -im, re) = (A, iA);
+ * a b-form entry is (re, -im, im, re) = (conj A, i conj A).  With them a complex
+ * multiply-add is two packed FP32x2 FMAs with one broadcast operand.
+ * qsvm_mps_bytes() is the size of a whole buffer.  The layout is private to
+ * this library: produce it with qsvm_build_mps. */
 size_t qsvm_mps_record_bytes(int32_t reps, int32_t precision);
 size_t qsvm_mps_bytes(int32_t n_qubits, int32_t reps, int64_t n_points, int32_t precision);
 
@@ -105,10 +115,11 @@ size_t qsvm_mps_bytes(int32_t n_qubits, int32_t reps, int64_t n_points, int32_t 
  *              scaled pixels, Sec. 3.2).
  *   precision  storage format of the output records (the build itself is FP64).
  *   mps        device output, at least qsvm_mps_bytes(...) bytes (mps_bytes).
- * Gate by gate in FP64, site by site: H and RZ act on the physical index; the
- * commuting CNOT.RZ.CNOT blocks of one repetition act as a bond-2 diagonal MPO
- * that copies each spin onto the bond and applies exp(-i theta Z_k Z_{k+1}),
- * theta = (pi - x_k)(pi - x_{k+1}), on the right-hand site.
+ * In FP64, site by site.  reps = 1, 3: gate by gate (H and RZ act on the physical
+ * index; the commuting CNOT.RZ.CNOT blocks of one repetition act as a bond-2
+ * diagonal MPO that copies each spin onto the bond and applies
+ * exp(-i theta Z_k Z_{k+1}), theta = (pi - x_k)(pi - x_{k+1}), on the right-hand
+ * site).  reps = 2: the three phases of the site, each from its angle.
  * Errors: QSVM_ERR_ARG (null, n_qubits < 2, n_points < 1, mps_bytes too small,
  * misaligned), QSVM_ERR_CHI (reps outside 1..3), QSVM_ERR_CUDA. */
 int32_t qsvm_build_mps(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
