@@ -75,7 +75,7 @@ FMA_PER_CMAC = {"fp32": 4, "fp32_split": 12, "fp64": 4}
 # same configuration with the default pipeline shape (dram__bytes_read.sum +
 # dram__bytes_write.sum; profiles/pair_tile_split_n784_r2.md).  Configurations
 # not captured with the current kernel report null.
-MEASURED_TRAFFIC_BYTES = {("gram_n784_r2_N8192", "fp32_split"): 40_496_324_096 + 559_182_080}
+MEASURED_TRAFFIC_BYTES = {("gram_n784_r2_N8192", "fp32_split"): 40_472_972_032 + 557_163_264}
 
 
 class ClockSampler:

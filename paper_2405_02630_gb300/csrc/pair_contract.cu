@@ -16,12 +16,12 @@ static const PipeShape kShapes[] = {{512, 4},  {1024, 3}, {512, 3},  {1024, 2}, 
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 
 // Defaults from shape sweeps on one GB300 (n = 784, N = 8192 Grams, reps = 2 in
-// phase form): split FP32 two stages of six sites (561 ms; three stages of two:
-// 685 ms), plain FP32 two stages of fifteen (150 ms), the chi = 8 kernels two
+// phase form): split FP32 two stages of seven sites (553 ms; three stages of two:
+// 680 ms), plain FP32 two stages of fifteen (150 ms), the chi = 8 kernels two
 // stages of 1 KB; FP64 is insensitive.  Two stages keep two CTAs per SM and the
 // longer chunks pay the per-chunk wait and hand-off less often.
 int default_shape(int chi, int prec) {
-  if (chi == 4 && prec == QSVM_FP32_SPLIT) return 8;
+  if (chi == 4 && prec == QSVM_FP32_SPLIT) return 9;
   if (chi == 4 && prec == QSVM_FP32) return 9;
   return (prec == QSVM_FP32 || chi >= 8) ? 3 : 1;
 }

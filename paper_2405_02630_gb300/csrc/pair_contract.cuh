@@ -1306,10 +1306,17 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
     if (valid || TPP > 1) {
       const uint32_t pa = base + slotA * SLOT;
       const uint32_t pb = base + slotB * SLOT;
+      if constexpr (PREC == QSVM_FP32_SPLIT && TPP == 1) {
+        // two sites per iteration let the compiler start a site's shared loads
+        // during the previous site's renormalisation (within the register budget)
+#pragma unroll 2
+        for (int s = 0; s < ns; ++s) eng.site(pa + s * Rec::kBytes, pb + s * Rec::kBytes);
+      } else {
 #pragma unroll 1
-      for (int s = 0; s < ns; ++s) {
-        eng.site(pa + s * Rec::kBytes, pb + s * Rec::kBytes);
-        if (Eng::kRenormEvery > 1 && ((k0 + s + 1) % Eng::kRenormEvery) == 0) eng.renorm();
+        for (int s = 0; s < ns; ++s) {
+          eng.site(pa + s * Rec::kBytes, pb + s * Rec::kBytes);
+          if (Eng::kRenormEvery > 1 && ((k0 + s + 1) % Eng::kRenormEvery) == 0) eng.renorm();
+        }
       }
     }
     __syncwarp();
