@@ -1,0 +1,81 @@
+"""CPU checks of the site-tensor structure the CUDA contraction relies on, on the
+oracle's dense closed-form tensors (oracle.mps_closed_form: A[k, sigma, t, u], layer
+m of a bond index in bit m-1, so the last layer is the HIGH bit there).
+
+1. The last layer is diagonal: A^sigma[t][u] = 0 unless the last-layer bit of u is sigma.
+2. The left neighbour's last-layer spin c enters only through the last ZZ phase:
+   rows with c = 1 equal the rows with c = 0 times exp(2 i theta z(sigma)).
+3. At reps = 2 every entry is +-1/2 times 1, T^2, P^2 or P^2 T^2 or a conjugate
+   (P = exp(-i x_k), T = exp(-i theta_{k-1})), in the pattern the phase-form records
+   encode, and contracting with that pattern reproduces the state-vector kernel.
+"""
+import numpy as np
+import pytest
+
+from paper_2405_02630_gb300 import inputs
+
+
+def _theta(x):
+    th = np.zeros_like(x)
+    th[1:] = (np.pi - x[:-1]) * (np.pi - x[1:])
+    return th
+
+
+@pytest.mark.parametrize("reps", [1, 2, 3])
+def test_last_layer_diagonal_and_row_factorisation(oracle, reps):
+    n = 7
+    x = inputs.uniform_features(1, n, 300 + reps)[0]
+    A = oracle.mps_closed_form(x, reps)
+    chi, H = 2 ** reps, 2 ** (reps - 1)
+    th = _theta(x)
+    for k in range(n):
+        for sigma in range(2):
+            for u in range(chi):
+                if (u >> (reps - 1)) != sigma and k < n - 1:
+                    assert np.all(A[k, sigma, :, u] == 0)
+            if k == 0:
+                continue
+            r = np.exp(2j * th[k] * (1 - 2 * sigma))
+            rows0, rows1 = A[k, sigma, :H, :], A[k, sigma, H:, :]  # last-layer bit c = 0 / 1
+            assert np.max(np.abs(rows1 - r * rows0)) <= 1e-14
+
+
+def test_reps2_phase_form(oracle):
+    n = 9
+    x = inputs.mnist_like_features(1, n, 310)[0]
+    A = oracle.mps_closed_form(x, 2)
+    th = _theta(x)
+    for k in range(n - 1):  # the oracle sums the last site's right bond
+        P2, T2 = np.exp(-2j * x[k]), np.exp(-2j * th[k])
+        V0, V1, V2 = T2, P2, P2 * T2
+        # blocks a_0s[q][p] = A[s][t = (q, c = 0)][u = (p, s)]; in the oracle's bit order
+        # layer 1 is bit 0 and layer 2 (the last) bit 1, so t = q + 2c and u = p + 2s.
+        # Site 0 has only t = 0 (its other rows meet a zero environment in the contraction).
+        rows = 1 if k == 0 else 2
+        for s, want in ((0, [[V2, 1], [V1, V0]]), (1, [[1, -np.conj(V2)], [np.conj(V0), -np.conj(V1)]])):
+            blk = np.array([[A[k, s, q, p + 2 * s] for p in range(2)] for q in range(rows)])
+            assert np.max(np.abs(blk - 0.5 * np.array(want)[:rows])) <= 1e-14, (k, s)
+
+
+def test_reps2_phase_form_contraction(oracle):
+    """Contract two points with the phase-form update (open last bond, amplitude = sum of
+    all entries) and compare with the state-vector kernel."""
+    n = 8
+    X = inputs.uniform_features(2, n, 320)
+    def ph(x):
+        th = _theta(x)
+        return np.exp(-2j * th), np.exp(-2j * x), np.exp(-2j * (x + th))
+    (V0, V1, V2), (W0, W1, W2) = ph(X[0]), ph(X[1])
+    E = [np.zeros((2, 2), complex), np.zeros((2, 2), complex)]
+    E[0][0, 0] = 1.0
+    for k in range(n):
+        a = [0.5 * np.array([[V2[k], 1], [V1[k], V0[k]]]),
+             0.5 * np.array([[1, -np.conj(V2[k])], [np.conj(V0[k]), -np.conj(V1[k])]])]
+        b = [0.5 * np.array([[W2[k], 1], [W1[k], W0[k]]]),
+             0.5 * np.array([[1, -np.conj(W2[k])], [np.conj(W0[k]), -np.conj(W1[k])]])]
+        rho0 = np.conj(V0[k]) * W0[k]
+        rho = [rho0, np.conj(rho0)]
+        E = [a[s].T @ (E[0] + rho[s] * E[1]) @ np.conj(b[s]) for s in range(2)]
+    K = abs(E[0].sum() + E[1].sum()) ** 2
+    Ko, _ = oracle.sv_kernel_pair(X[0], X[1], 2)
+    assert abs(K - Ko) <= 1e-13
