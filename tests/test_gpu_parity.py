@@ -177,8 +177,11 @@ def test_gram_vs_mps_oracle(q, oracle, prec, reps, N, n):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_split", "fp32"])
-def test_cross_vs_mps_oracle(q, oracle, prec):
-    n, reps = 64, 2
+@pytest.mark.parametrize("reps", [1, 2, 3])
+def test_cross_vs_mps_oracle(q, oracle, prec, reps):
+    """Test x train with n_a != n_b, so a wrong column-side (b-form) offset in the
+    two-array block formats (reps 1, 3) would show."""
+    n = 64
     Xtr = inputs.uniform_features(53, n, 11)
     Xte = inputs.uniform_features(29, n, 12)
     Ko, LKo = oracle.mps_cross(Xte, Xtr, reps)
