@@ -11,18 +11,21 @@ struct PipeShape {
   int chunk_bytes;
   int stages;
 };
-static const PipeShape kShapes[] = {{512, 4},  {1024, 3}, {512, 3},  {1024, 2}, {1024, 4},
-                                    {2048, 2}, {2048, 3}, {512, 2},  {1152, 2}, {1440, 2}};
+static const PipeShape kShapes[] = {{512, 4},  {1024, 3}, {512, 3},  {1024, 2}, {1024, 4},  {2048, 2},
+                                    {2048, 3}, {512, 2},  {1152, 2}, {1440, 2}, {2304, 2}, {3456, 2}};
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 
-// Defaults from shape sweeps on one GB300 (n = 784, N = 8192 Grams, reps = 2 in
-// phase form): split FP32 two stages of seven sites (553 ms; three stages of two:
-// 680 ms), plain FP32 two stages of fifteen (150 ms), the chi = 8 kernels two
-// stages of 1 KB; FP64 is insensitive.  Two stages keep two CTAs per SM and the
-// longer chunks pay the per-chunk wait and hand-off less often.
+// Defaults from shape sweeps on one GB300 (n = 784 Grams): at reps = 2 (phase
+// form, N = 8192) split FP32 two stages of seven sites (553 ms; three stages of
+// two: 680 ms) and plain FP32 two stages of fifteen (150 ms); at reps = 3
+// (N = 2048) the four-thread split kernel two stages of two sites (302 ms; one
+// site per chunk: 336 ms; three sites leave one CTA per SM: 334 ms).  FP64 is
+// insensitive.  Two stages keep two CTAs per SM and the longer chunks pay the
+// per-chunk wait and hand-off less often.
 int default_shape(int chi, int prec) {
   if (chi == 4 && prec == QSVM_FP32_SPLIT) return 9;
   if (chi == 4 && prec == QSVM_FP32) return 9;
+  if (chi >= 8 && prec == QSVM_FP32_SPLIT) return 10;
   return (prec == QSVM_FP32 || chi >= 8) ? 3 : 1;
 }
 
