@@ -1,18 +1,21 @@
 #!/usr/bin/env python
-"""Benchmark: quantum-kernel Gram entries/s on one GB300 (or N GPUs, strong scaling).
+"""Benchmark: quantum-kernel Gram entries/s on one GB300 (or G GPUs, weak scaling).
 
 Workload (default): n = 784 qubits (28 x 28 MNIST-like features, 80 % exact zeros,
 the rest uniform on (0, 1] * pi; seed 4), reps = 2 (bond dimension 4),
 N = 8192 points, the full symmetric 8192 x 8192 Gram.  One step = the whole hot
-path: MPS build from the feature matrix (FP64, gate by gate) + the all-pairs
-contraction over the upper-triangle tiles (diagonal included) + the mirror
-write.  Entries counted = unique pairs contracted, N (N + 1) / 2 per step.
+path: MPS build from the feature matrix (FP64; at reps = 2 the three unit phases
+of every site) + the all-pairs contraction over the upper-triangle tiles
+(diagonal included) + the mirror write.  Entries counted = unique pairs
+contracted, N (N + 1) / 2 per step.
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
 the launching stream with a synchronize on both sides; the L2 (129 MB) is
-flushed by writing a 512 MB buffer between timed steps.  Under torchrun each
-rank computes a contiguous, pair-balanced share of the tiles of the same Gram
-(strong scaling, no collective on the data path); the time is the max over ranks.
+flushed by writing a 512 MB buffer between timed steps.  Under torchrun with G
+ranks the Gram grows to round(N sqrt(G)) points (same distribution and seed), so
+each rank's contiguous, pair-balanced share of its tiles stays the size of the
+one-GPU Gram (weak scaling, no collective on the data path); the time is the max
+over ranks and the value counts the pairs of all ranks.
 
 --impl reference times the CPU oracle (plain FP64 C, closed-form MPS overlap,
 OpenMP over pairs) on the host cores on a bounded random sample of the same
@@ -175,7 +178,7 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": "gram_entries_per_s", "value": value, "unit": "entries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
-        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_qubits": n, "reps": reps, "n_points": N,
                    "entries": "unique pairs i<=j", "note": "CPU oracle on a random sample of pairs per step"},
         "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores, "kind": "oracle",
@@ -233,7 +236,7 @@ def run_ours(args):
     qbuild.build()
     qsvm.lib()
 
-    X, Xte, n, reps = inputs.workload(args.workload)
+    X, Xte, n, reps = inputs.workload(args.workload, scale=world ** 0.5)
     N = X.shape[0]
     Nte = 0 if Xte is None else Xte.shape[0]
     prec = args.precision
@@ -343,10 +346,11 @@ def run_ours(args):
     line = {
         "metric": "gram_entries_per_s", "value": value, "unit": "entries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "strong", "vs_baseline": None, "dtype": {"fp32_split": "f32x2-split", "fp32": "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32_split": "f32x2-split", "fp32": "f32",
                                                             "fp64": "f64"}[prec],
         "data": "synthetic",
         "config": {"workload": args.workload, "n_qubits": n, "reps": reps, "n_points": N, "n_test": Nte,
+                   "points_scaled_by": round(world ** 0.5, 6),
                    "precision": prec,
                    "entries": "unique Gram pairs i<=j incl. diagonal" + (" + test x train" if Nte else ""),
                    "l2": "flushed (512 MB write) between timed steps", "parallelism": f"tiles{world}"},

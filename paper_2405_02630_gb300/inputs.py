@@ -41,9 +41,13 @@ def mnist_like_features(n_points: int, n_features: int, seed: int, p_zero: float
     return np.where(zero, 0.0, val)
 
 
-def workload(name: str):
-    """Returns (X_train, X_test or None, n_qubits, reps) for a named workload."""
+def workload(name: str, scale: float = 1.0):
+    """Returns (X_train, X_test or None, n_qubits, reps) for a named workload.  ``scale``
+    multiplies the numbers of points (same distribution and seed), e.g. by sqrt(G) to
+    keep the pairs per GPU fixed when a Gram is shared by G GPUs."""
     n, reps, ntr, nte, kind, seed = WORKLOADS[name]
+    if scale != 1.0:
+        ntr, nte = int(round(ntr * scale)), int(round(nte * scale))
     gen = uniform_features if kind == "uniform" else mnist_like_features
     X = gen(ntr + nte, n, seed)
     return X[:ntr], (X[ntr:] if nte else None), n, reps

@@ -172,3 +172,19 @@ def test_statevector_sizes_and_errors():
     assert L.qsvm_sv_gram(v(64), 4, 8, 0, v(64), 4, v(64), 1 << 30, None) == qsvm.QSVM_ERR_ARG
     assert L.qsvm_sv_gram(v(64), 4, 8, 2, v(64), 3, v(64), 1 << 30, None) == qsvm.QSVM_ERR_ARG
     assert L.qsvm_sv_gram(v(64), 4, 8, 2, v(64), 4, v(64), 100, None) == qsvm.QSVM_ERR_WORKSPACE
+
+
+def test_weak_scaling_workload_sizes():
+    """The bench's G-rank run grows the Gram to round(N sqrt(G)) points, so every rank's
+    pair-balanced share stays near the one-GPU Gram's pair count."""
+    from paper_2405_02630_gb300 import inputs
+    N = inputs.WORKLOADS["gram_n784_r2_N8192"][2]
+    for G in (1, 2, 4, 8):
+        Ng = int(round(N * G ** 0.5))
+        X, Xte, n, reps = inputs.workload("cfg0_n8_r2_N16", scale=G ** 0.5)
+        assert X.shape == (int(round(16 * G ** 0.5)), 8) and Xte is None
+        total = qsvm.qsvm_gram_num_tiles(Ng, reps, "fp32_split")
+        shares = [qsvm.qsvm_gram_partition(Ng, reps, "fp32_split", G, r) for r in range(G)]
+        assert shares[0][0] == 0 and shares[-1][1] == total
+        per_rank_pairs = Ng * (Ng + 1) / 2 / G
+        assert abs(per_rank_pairs / (N * (N + 1) / 2) - 1) < 1e-3
