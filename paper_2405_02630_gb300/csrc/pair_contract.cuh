@@ -13,7 +13,9 @@
 // repetition's ZZ phase, so a_1s = r_s a_0s with r_0 = exp(2 i theta_{k-1}) and
 // r_1 = conj(r_0) (the record stores a_0s and r).  Hence
 //     E'_s = a_0s^T (E_0 + rho_s E_1) conj(b_0s),   rho_s = r_s(i) conj(r_s(j)),
-// chi^3/2 + chi^2/2 + 1 complex MACs per site instead of chi^3.
+// chi^3/2 + chi^2/2 + 1 complex MACs per site instead of chi^3.  At reps = 2 the
+// site tensors are generated in registers from three unit phases per site (the
+// phase form, below): 33 complex MACs per site.
 //
 // One CTA owns a TI x TI tile of pairs, one thread per pair, E in registers for
 // all n sites.  The tile's 2*TI points stream their site records through shared
