@@ -4,8 +4,8 @@
 Workload (default): n = 784 qubits (28 x 28 MNIST-like features, 80 % exact zeros,
 the rest uniform on (0, 1] * pi; seed 4), reps = 2 (bond dimension 4),
 N = 8192 points, the full symmetric 8192 x 8192 Gram.  One step = the whole hot
-path: MPS build from the feature matrix (FP64; at reps = 2 the three unit phases
-of every site) + the all-pairs contraction over the upper-triangle tiles
+path: MPS build from the feature matrix (FP64, gate by gate; at reps = 2 stored
+as the three unit phases of every site) + the all-pairs contraction over the upper-triangle tiles
 (diagonal included) + the mirror write.  Entries counted = unique pairs
 contracted, N (N + 1) / 2 per step.
 

@@ -119,7 +119,8 @@ size_t qsvm_mps_bytes(int32_t n_qubits, int32_t reps, int64_t n_points, int32_t 
  * index; the commuting CNOT.RZ.CNOT blocks of one repetition act as a bond-2
  * diagonal MPO that copies each spin onto the bond and applies
  * exp(-i theta Z_k Z_{k+1}), theta = (pi - x_k)(pi - x_{k+1}), on the right-hand
- * site).  reps = 2: the three phases of the site, each from its angle.
+ * site).  reps = 2: the same gates applied to the rows t = 0, 2 (right bond open),
+ * and the three phases read off three of the resulting entries.
  * Errors: QSVM_ERR_ARG (null, n_qubits < 2, n_points < 1, mps_bytes too small,
  * misaligned), QSVM_ERR_CHI (reps outside 1..3), QSVM_ERR_CUDA. */
 int32_t qsvm_build_mps(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,

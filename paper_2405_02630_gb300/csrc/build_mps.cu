@@ -118,9 +118,9 @@ __device__ __forceinline__ void site_row(int t, bool has_left, cd rz0, cd zzp, c
 // (z(b) = 1 - 2b; the two RZ layers, the two ZZ layers with the left neighbour's
 // layer spins q, c, and the Hadamard sign between the layers), so with
 // P = e^{-i x_k}, T = e^{-i theta_{k-1}} every entry is +-1/2 times one of 1,
-// T^2, P^2, P^2 T^2 or a conjugate: the record keeps those three phases, each
-// evaluated directly from its angle.  The last site keeps the same tensor with
-// its right bond open (the contraction sums it at the end).
+// T^2, P^2, P^2 T^2 or a conjugate: the record keeps those three phases, read off
+// the entries the gate-by-gate build produces.  The last site keeps the same
+// tensor with its right bond open (the contraction sums it at the end).
 template <int PREC>
 __device__ __forceinline__ void store_phase(uint8_t* rec, int v, cd z) {
   using Rec = Record<4, PREC>;
@@ -137,12 +137,6 @@ __device__ __forceinline__ void store_phase(uint8_t* rec, int v, cd z) {
   }
 }
 
-__device__ __forceinline__ cd unit_phase(double a) {  // e^{-i a}
-  double sn, cs;
-  sincos(a, &sn, &cs);
-  return cd{cs, -sn};
-}
-
 template <int R, int PREC>
 __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict__ X, int64_t n_points, int n,
                                                         uint8_t* __restrict__ mps) {
@@ -153,25 +147,37 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
   const int64_t i = gid / n;
   const int k = (int)(gid - i * n);
   const double xk = X[i * n + k];
+  double sx, cx;
+  sincos(xk, &sx, &cx);
+  const cd rz0 = cd{cx, -sx};  // e^{-i x_k}
+  cd zzp = cd{1.0, 0.0}, zzm = cd{1.0, 0.0};
+  const bool has_left = k > 0;
+  if (has_left) {
+    const double th = (kPi - X[i * n + k - 1]) * (kPi - xk);
+    double st, ct;
+    sincos(th, &st, &ct);
+    zzp = cd{ct, -st};  // a = 0: z(a) = +1 -> exp(-i theta) for sigma = 0
+    zzm = cd{ct, st};   // a = 1: z(a) = -1 -> exp(+i theta) for sigma = 0
+  }
   if constexpr (R == 2) {
-    const double th = k > 0 ? (kPi - X[i * n + k - 1]) * (kPi - xk) : 0.0;
-    uint8_t* rec = mps + gid * Record<4, PREC>::kBytes;
-    store_phase<PREC>(rec, 0, unit_phase(2.0 * th));
-    store_phase<PREC>(rec, 1, unit_phase(2.0 * xk));
-    store_phase<PREC>(rec, 2, unit_phase(2.0 * (xk + th)));
-  } else {
-    double sx, cx;
-    sincos(xk, &sx, &cx);
-    const cd rz0 = cd{cx, -sx};  // e^{-i x_k}
-    cd zzp = cd{1.0, 0.0}, zzm = cd{1.0, 0.0};
-    const bool has_left = k > 0;
+    // Apply the site's gates to rows t = 0 and t = 2 (right bond open, also at the
+    // last site) and read the three phases off the entries a_00[0][0] = V2 / 2,
+    // a_00[1][0] = V1 / 2, a_00[1][1] = V0 / 2.  Site 0 has only t = 0; there
+    // T = 1, so V0 = 1 and V1 = V2.
+    cd v[2][CHI];
+    site_row<R, false>(0, has_left, rz0, zzp, zzm, v);
+    const cd V2 = cd{2.0 * v[0][0].re, 2.0 * v[0][0].im};
+    cd V1 = V2, V0 = cd{1.0, 0.0};
     if (has_left) {
-      const double th = (kPi - X[i * n + k - 1]) * (kPi - xk);
-      double st, ct;
-      sincos(th, &st, &ct);
-      zzp = cd{ct, -st};  // a = 0: z(a) = +1 -> exp(-i theta) for sigma = 0
-      zzm = cd{ct, st};   // a = 1: z(a) = -1 -> exp(+i theta) for sigma = 0
+      site_row<R, false>(2, has_left, rz0, zzp, zzm, v);
+      V1 = cd{2.0 * v[0][0].re, 2.0 * v[0][0].im};
+      V0 = cd{2.0 * v[0][2].re, 2.0 * v[0][2].im};
     }
+    uint8_t* rec = mps + gid * Record<4, PREC>::kBytes;
+    store_phase<PREC>(rec, 0, V0);
+    store_phase<PREC>(rec, 1, V1);
+    store_phase<PREC>(rec, 2, V2);
+  } else {
     uint8_t* recA = mps + gid * Rec::kBytes;
     uint8_t* recB = recA + (Rec::kForms == 2 ? n_points * (int64_t)n * Rec::kBytes : 0);
     const bool last = (k == n - 1);
