@@ -372,6 +372,7 @@ def run_ours(args):
         Ko, _ = oracle.mps_pairs(X, X, ia, ib, reps)
         Kg = K[torch.from_numpy(ia).to(dev), torch.from_numpy(ib).to(dev)].cpu().numpy()
         acc = {"pairs": int(ia.size), "max_abs_dK": float(np.max(np.abs(Kg - Ko))),
+               "mean_abs_dK": float(np.mean(np.abs(Kg - Ko))),
                "max_abs_diag_minus_1": float(np.max(np.abs(np.diag(K.cpu().numpy()) - 1)))}
         if Nte:
             xa, xb = rng.integers(0, Nte, ns), rng.integers(0, N, ns)
@@ -382,11 +383,15 @@ def run_ours(args):
         # near-duplicate pairs, K spread over (0, 1): where |dK| is informative
         base = inputs.mnist_like_features(24, n, 21) if n >= 64 else inputs.uniform_features(24, n, 21)
         pert = inputs.near_duplicates(base, 22)
-        Knd_o, _ = oracle.mps_cross(base, pert, reps)
-        Knd, _ = qsvm.cross(torch.from_numpy(base).to(dev), torch.from_numpy(pert).to(dev), reps, prec)
+        Knd_o, LKnd_o = oracle.mps_cross(base, pert, reps)
+        Knd, LKnd = qsvm.cross(torch.from_numpy(base).to(dev), torch.from_numpy(pert).to(dev), reps, prec, logK=True)
         d = np.abs(Knd.cpu().numpy() - Knd_o)
+        big = Knd_o > 1e-300  # log10 K compared where the oracle's K is a normal double
+        dlog10 = np.abs(LKnd.cpu().numpy() - LKnd_o)[big] / np.log(10.0)
         acc["near_dup"] = {"pairs": int(d.size), "K_range": [float(Knd_o.min()), float(Knd_o.max())],
-                           "max_abs_dK": float(d.max()), "mean_abs_dK": float(d.mean())}
+                           "max_abs_dK": float(d.max()), "mean_abs_dK": float(d.mean()),
+                           "max_abs_dlog10K": float(dlog10.max()) if dlog10.size else None,
+                           "log_pairs": int(dlog10.size)}
         line["accuracy_vs_oracle"] = acc
         # the FP64 path on the same GPU, on the first tiles of the same Gram (speedup report)
         if prec != "fp64":
