@@ -269,6 +269,24 @@ def run_ours(args):
     pairs_rank = tiles_pairs(tb, te) + (a1 - a0) * N
     total_pairs = N * (N + 1) // 2 + Nte * N
 
+    # pipeline shape: the autotuner times every shape on a Gram of up to 4096 of the
+    # workload's points (untimed setup) and keeps the fastest for the timed steps
+    pipeline = {"autotuned": False}
+    if args.autotune:
+        Nt = min(N, 4096)
+        mps_t = torch.empty(qsvm.qsvm_mps_bytes(n, reps, Nt, P), dtype=torch.uint8, device=dev)
+        qsvm.qsvm_build_mps(Xd[:Nt].contiguous(), reps, P, mps=mps_t, stream=stream)
+        K_t = torch.empty((Nt, Nt), dtype=torch.float64, device=dev)
+        best, tune_ms = qsvm.qsvm_autotune(mps_t, Nt, n, reps, P, K_t, stream=stream)
+        torch.cuda.synchronize()
+        del mps_t, K_t
+        pipeline = {"autotuned": True, "tuned_on_points": Nt, "config": best,
+                    "tune_ms": [round(v, 3) for v in tune_ms]}
+    cfg = qsvm.qsvm_get_config(reps, P)  # -1: the library's default shape for (reps, precision)
+    pipeline["config"] = cfg
+    if cfg >= 0:
+        pipeline["sites_per_chunk"], pipeline["stages"] = qsvm.qsvm_config_info(cfg, reps, P)
+
     def step(prec_code=P, tile_range=(tb, te)):
         qsvm.qsvm_build_mps(Xd, reps, prec_code, mps=mps, stream=stream)
         if Nte:
@@ -355,6 +373,7 @@ def run_ours(args):
                    "entries": "unique Gram pairs i<=j incl. diagonal" + (" + test x train" if Nte else ""),
                    "l2": "flushed (512 MB write) between timed steps", "parallelism": f"tiles{world}"},
         "roofline": roofline,
+        "pipeline": pipeline,
         "gpu_launches": (4 if Nte else 2) * args.steps,
         "clocks": clocks,
         "pair_kernel_ms": kms,
@@ -595,6 +614,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the accuracy, FP64 and CPU side measurements")
     ap.add_argument("--full-fp64", action="store_true", help="compare every entry with the FP64 path (small N)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the pipeline shape with the autotuner (on up to 4096 points) before timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
