@@ -87,14 +87,22 @@ enum qsvm_precision {
  * The last site's tensor keeps its right bond open (its layer-1 spin is summed
  * by the contraction).  One array of records.
  *
- * Block form (reps = 1 and 3): the record stores the two chi/2 x chi/2 blocks
+ * Phase form, split FP32 at reps = 3: every entry of a chi = 8 site is
+ * +-2^{-3/2} P^A T^B with A, B in {3, 1, -1} (block 0) or the conjugate of one
+ * (block 1); the record holds W[3 ia + ib] = 2^{-3/2} P^{3 - 2 ia} T^{3 - 2 ib}
+ * (ia, ib in 0..2) and, as value 9, r = conj(T^2), each as its a-form then its
+ * b-form entry, the hi entries of the ten values then the lo entries, 640 bytes,
+ * one array; the last site keeps its right bond open.  With q = 2 q1 + q2 and
+ * p = 2 p1 + p2, a_00[q][p] = (-1)^{p1 p2} W[k] and
+ * a_01[q][p] = (-1)^{p1 p2 + p2} conj(W[8 - k]), k = 3 (p1 + p2) + (q1 ^ p1) + (q2 ^ p2).
+ *
+ * Block form (reps = 1; reps = 3 in FP64 and FP32): the record stores the two chi/2 x chi/2 blocks
  * a_00, a_01, each row-major over (q, p), then the phase r_0, 16 bytes per value:
  *   QSVM_FP64        (re, im) as two doubles;
  *   QSVM_FP32        one "form" entry of four floats;
  *   QSVM_FP32_SPLIT  per block: the chi^2/4 "hi" form entries (re and im on the
  *                    2^-11 grid), then the chi^2/4 "lo" form entries; the phase
- *                    as a hi entry then a lo entry; at reps = 3 each block is
- *                    followed by 16 unused bytes (shared-memory bank spreading).
+ *                    as a hi entry then a lo entry.
  * Site 0 has a left bond of dimension 1 (only t = 0 is nonzero); the last site
  * has a right bond of dimension 2 holding the physical index (u = sigma, p = 0).
  * The FP32 block formats hold two arrays of records: first the row-side a-forms,

@@ -17,15 +17,15 @@ constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 
 // Defaults from shape sweeps on one GB300 (n = 784 Grams): at reps = 2 (phase
 // form, N = 8192) split FP32 two stages of seven sites (553 ms; three stages of
-// two: 680 ms) and plain FP32 two stages of fifteen (150 ms); at reps = 3
-// (N = 2048) the four-thread split kernel two stages of two sites (302 ms; one
-// site per chunk: 336 ms; three sites leave one CTA per SM: 334 ms).  FP64 is
+// two: 680 ms) and plain FP32 two stages of fifteen (150 ms); at reps = 3 the
+// four-thread split kernel two stages of three 640-byte phase-form sites (two
+// CTAs per SM; with 1088-byte block records two sites per chunk had been best).  FP64 is
 // insensitive.  Two stages keep two CTAs per SM and the longer chunks pay the
 // per-chunk wait and hand-off less often.
 int default_shape(int chi, int prec) {
   if (chi == 4 && prec == QSVM_FP32_SPLIT) return 9;
   if (chi == 4 && prec == QSVM_FP32) return 9;
-  if (chi >= 8 && prec == QSVM_FP32_SPLIT) return 10;
+  if (chi >= 8 && prec == QSVM_FP32_SPLIT) return 5;
   return (prec == QSVM_FP32 || chi >= 8) ? 3 : 1;
 }
 

@@ -961,9 +961,13 @@ __device__ int32_t g_pair_status;
 // E_1, publishes them in a padded shared buffer, reads all of G_s back (every
 // row is needed: X[p][r] = sum_q a[q][p] G_s[q][r]), builds its two rows of X,
 // accumulates its two rows of E'_s = X conj(b_0s) and writes them back; warp
-// barriers separate the reads and writes of the buffer.  The quad agrees on the
-// power-of-two rescale through two xor-shuffles.  Grids and products per entry
-// are those of Engine<8, QSVM_FP32_SPLIT>.
+// barriers separate the reads and writes of the buffer.  The site tensors come in
+// phase form (nine values W and r per site, see Record<8, QSVM_FP32_SPLIT>): the
+// row side reads the value of each of its eight entries, the column side reads
+// each of the nine values once and applies it to the entries that carry it, and
+// the signs of rows and columns are folded into the rescale.  The quad agrees on
+// the power-of-two rescale through two xor-shuffles.  The grids are those of the
+// block form at chi = 8 (the stored values keep the factor 2^{-3/2}).
 template <int PREC>
 struct QuadEngine;
 
@@ -1002,11 +1006,27 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
     return reinterpret_cast<float4*>(ebuf + (c * 16 + q * 4 + (r ^ (2 * c + (q >> 1)))) * 4);
   }
 
+  // slot k = 3 ia + ib of entry (r, pp) of b_0s (and of (q, p) of a_0s): ia = p1 + p2,
+  // ib = (q1 ^ p1) + (q2 ^ p2) with q = 2 q1 + q2, p = 2 p1 + p2
+  static __host__ __device__ constexpr int slot(int q, int p) {
+    return 3 * ((p >> 1) + (p & 1)) + (((q >> 1) ^ (p >> 1)) + ((q & 1) ^ (p & 1)));
+  }
+
+  static __device__ __forceinline__ void load_value(uint32_t rec, int v, int f, float2& vh, float2& ivh, float2& vl,
+                                                    float2& ivl) {
+    const float4 qh = *reinterpret_cast<const float4*>(sptr(rec + Rec::off(v, f, 0)));
+    const float4 ql = *reinterpret_cast<const float4*>(sptr(rec + Rec::off(v, f, 1)));
+    vh = make_float2(qh.x, qh.y);
+    ivh = make_float2(qh.z, qh.w);
+    vl = make_float2(ql.x, ql.y);
+    ivl = make_float2(ql.z, ql.w);
+  }
+
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     const float2 m1 = make_float2(-1.f, -1.f);
     float2 Rh[2], iRh[2], Rl[2], iRl[2];
-    split_phase(ra + Rec::kPhaseOff, ra + Rec::kPhaseOff + 16, rb + Rec::kPhaseOff, rb + Rec::kPhaseOff + 16, Rh, iRh,
-                Rl, iRl);
+    split_phase(ra + Rec::off(9, 0, 0), ra + Rec::off(9, 0, 1), rb + Rec::off(9, 1, 0), rb + Rec::off(9, 1, 1), Rh,
+                iRh, Rl, iRl);
     const float2 rh = s ? Rh[1] : Rh[0], irh = s ? iRh[1] : iRh[0];
     const float2 rl = s ? Rl[1] : Rl[0], irl = s ? iRl[1] : iRl[0];
     // own rows of G_s from the same rows of E_0 and E_1
@@ -1028,9 +1048,9 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
 #pragma unroll
       for (int r = 0; r < H; ++r) *entry(s, 2 * h + j, r) = Gq[j][r];
     __syncwarp(mask);  // G_0 and G_1 are complete
-    const uint32_t pa = ra + s * Rec::kBlockStride;
-    const uint32_t pb = rb + s * Rec::kBlockStride;
-    // X[p][r] = sum_q a[q][p] G_s[q][r] for the thread's two rows p
+    // X[p][r] = sum_q a[q][p] G_s[q][r] for the thread's two rows p = 2h + j, with the
+    // row signs of a_0s left out (applied in the rescale).  Block 0 uses W[k] (a-form),
+    // block 1 conj(W[8 - k]) (b-form).
     float2 Xh[2][H], Xl[2][H], Xf[2][H];
     {
       float2 hh[2][H], ll[2][H];
@@ -1043,12 +1063,8 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
         float2 Ah[2], iAh[2], Al[2], iAl[2];
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-          const float4 va = *reinterpret_cast<const float4*>(sptr(pa + (q * H + 2 * h + p) * 16));
-          const float4 vl = *reinterpret_cast<const float4*>(sptr(pa + Rec::kPartBytes + (q * H + 2 * h + p) * 16));
-          Ah[p] = make_float2(va.x, va.y);
-          iAh[p] = make_float2(va.z, va.w);
-          Al[p] = make_float2(vl.x, vl.y);
-          iAl[p] = make_float2(vl.z, vl.w);
+          const int k = slot(q, 2 * h + p);
+          load_value(ra, s ? 8 - k : k, s, Ah[p], iAh[p], Al[p], iAl[p]);
         }
 #pragma unroll
         for (int r = 0; r < H; ++r) {
@@ -1077,32 +1093,36 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
           Xf[p][r] = v;
         }
     }
-    // E'_s[p][pp] = sum_r X[p][r] conj(b[r][pp])
+    // E'_s[p][pp] = sum_r X[p][r] conj(b[r][pp]), column signs left out: conj(b_00) uses
+    // conj(W[k]) (b-form), conj(b_01) uses W[8 - k] (a-form).  Each of the nine values is
+    // loaded once and applied to the entries (r, pp) of its slot.
     float2 Nh[2][H], Nl[2][H];
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
       for (int pp = 0; pp < H; ++pp) Nh[p][pp] = Nl[p][pp] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int r = 0; r < H; ++r) {
+    for (int k = 0; k < 9; ++k) {
+      float2 Bh, iBh, Bl, iBl;
+      load_value(rb, s ? 8 - k : k, 1 - s, Bh, iBh, Bl, iBl);
 #pragma unroll
-      for (int pp = 0; pp < H; ++pp) {
-        const float4 vb = reinterpret_cast<const float4*>(sptr(pb + (r * H + pp) * 16))[0];
-        const float4 vl = reinterpret_cast<const float4*>(sptr(pb + Rec::kPartBytes + (r * H + pp) * 16))[0];
-        const float2 Bh = make_float2(vb.x, vb.y), iBh = make_float2(vb.z, vb.w);
-        const float2 Bl = make_float2(vl.x, vl.y), iBl = make_float2(vl.z, vl.w);
+      for (int r = 0; r < H; ++r)
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          Nh[p][pp] = fma2(bc(Xh[p][r].x), Bh, Nh[p][pp]);
-          Nh[p][pp] = fma2(bc(Xh[p][r].y), iBh, Nh[p][pp]);
-          Nl[p][pp] = fma2(bc(Xf[p][r].x), Bl, Nl[p][pp]);
-          Nl[p][pp] = fma2(bc(Xf[p][r].y), iBl, Nl[p][pp]);
-          Nl[p][pp] = fma2(bc(Xl[p][r].x), Bh, Nl[p][pp]);
-          Nl[p][pp] = fma2(bc(Xl[p][r].y), iBh, Nl[p][pp]);
+        for (int pp = 0; pp < H; ++pp) {
+          if (slot(r, pp) != k) continue;
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            Nh[p][pp] = fma2(bc(Xh[p][r].x), Bh, Nh[p][pp]);
+            Nh[p][pp] = fma2(bc(Xh[p][r].y), iBh, Nh[p][pp]);
+            Nl[p][pp] = fma2(bc(Xf[p][r].x), Bl, Nl[p][pp]);
+            Nl[p][pp] = fma2(bc(Xf[p][r].y), iBl, Nl[p][pp]);
+            Nl[p][pp] = fma2(bc(Xl[p][r].x), Bh, Nl[p][pp]);
+            Nl[p][pp] = fma2(bc(Xl[p][r].y), iBh, Nl[p][pp]);
+          }
         }
-      }
     }
-    // quad-wide rescale by 2^-e, then split onto the E grid
+    // quad-wide rescale by 2^-e with the signs (-1)^{p1 p2 + p2 s} of row p and of
+    // column pp, then split onto the E grid
     float2 V[2][H];
 #pragma unroll
     for (int p = 0; p < 2; ++p)
@@ -1128,15 +1148,17 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
         e += 100;
       }
     }
-    const float2 sc = bc(pow2f(-e));
+    const float sc = pow2f(-e);
     __syncwarp(mask);  // every thread of the warp has read G
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
       for (int pp = 0; pp < H; ++pp) {
-        const float2 f = mul2(V[p][pp], sc);
+        const int neg = ((h & p) ^ (p & s) ^ ((pp >> 1) & pp & 1) ^ (pp & 1 & s)) & 1;
+        const float2 scs = bc(neg ? -sc : sc);
+        const float2 f = mul2(V[p][pp], scs);
         const float2 hv = grid_round2<kGridE>(f);
-        const float2 lv = fma2(Nl[p][pp], sc, fma2(hv, m1, mul2(Nh[p][pp], sc)));
+        const float2 lv = fma2(Nl[p][pp], scs, fma2(hv, m1, mul2(Nh[p][pp], scs)));
         *entry(s, 2 * h + p, pp) = make_float4(hv.x, hv.y, lv.x, lv.y);
       }
     __syncwarp(mask);  // the new environment is complete before anyone reads it
@@ -1145,12 +1167,18 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
 
   __device__ __forceinline__ void renorm() {}
 
-  // amplitude = E_0[0][0] + E_1[0][0] (both in the shared buffer after the last site)
+  // the last site keeps its right bond open: amplitude = sum of all entries of E
   __device__ __forceinline__ void amplitude(double& re, double& im) const {
-    const float4 a = *entry(0, 0, 0);
-    const float4 b = *entry(1, 0, 0);
-    re = __dadd_rn(__dadd_rn((double)a.x, (double)a.z), __dadd_rn((double)b.x, (double)b.z));
-    im = __dadd_rn(__dadd_rn((double)a.y, (double)a.w), __dadd_rn((double)b.y, (double)b.w));
+    re = 0.0;
+    im = 0.0;
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c)
+      for (int q = 0; q < H; ++q)
+        for (int r = 0; r < H; ++r) {
+          const float4 v = *entry(c, q, r);
+          re = __dadd_rn(re, __dadd_rn((double)v.x, (double)v.z));
+          im = __dadd_rn(im, __dadd_rn((double)v.y, (double)v.w));
+        }
   }
 };
 

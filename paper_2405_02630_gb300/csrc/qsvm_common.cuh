@@ -26,7 +26,7 @@ constexpr int kGridE = 10;
 constexpr int kGridG = 10;
 __host__ __device__ constexpr int grid_x(int chi) { return chi >= 8 ? 9 : 10; }
 
-// Site-record geometry, block form (reps = 1 and 3).  A record holds the blocks
+// Site-record geometry, block form (reps = 1; reps = 3 in FP64 and FP32).  A record holds the blocks
 // a_00 and a_01 (16 bytes per complex entry) and then the phase entry r.  FP64
 // records hold each value once as (re, im).  The FP32 formats hold two forms of
 // every record, in two arrays (all row-side "a-form" records of the buffer first,
@@ -46,10 +46,7 @@ struct Record {
   static constexpr int kParts = (PREC == QSVM_FP32_SPLIT) ? 2 : 1;
   static constexpr int kPartBytes = kEntries * kEntryBytes;
   static constexpr int kBlockBytes = kPartBytes * kParts;
-  // Split FP32 at chi = 8 is read by four threads per pair, which load the same
-  // entry of both blocks at once: 16 bytes between the blocks put those reads in
-  // different shared-memory bank groups.
-  static constexpr int kBlockStride = kBlockBytes + ((CHI >= 8 && PREC == QSVM_FP32_SPLIT) ? 16 : 0);
+  static constexpr int kBlockStride = kBlockBytes;
   static constexpr int kPhaseOff = 2 * kBlockStride;   // phase r: one entry per part
   static constexpr int kBytes = kPhaseOff + kParts * kEntryBytes;  // one form of one site
 };
@@ -74,10 +71,28 @@ struct Record<4, PREC> {
   __host__ __device__ static constexpr int off(int v, int f, int part) { return part * kPartBytes + v * kValBytes + f * 16; }
 };
 
+// Phase form for split FP32 at reps = 3.  Every entry of a chi = 8 site is
+// +-2^{-3/2} P^A T^B with A, B in {3, 1, -1} (block 0) or the conjugate of one
+// (block 1); the record holds W[3 ia + ib] = 2^{-3/2} P^{3 - 2 ia} T^{3 - 2 ib}
+// (ia, ib in 0..2) and, as value 9, r = e^{2 i theta_{k-1}}: per value its a-form
+// then its b-form entry, the hi entries of all ten values, then the lo entries.
+// With q = 2 q1 + q2 and p = 2 p1 + p2 (layer 1 in the high bit):
+//   a_00[q][p] = (-1)^{p1 p2}        W[k],            k = 3 (p1 + p2) + (q1 ^ p1) + (q2 ^ p2),
+//   a_01[q][p] = (-1)^{p1 p2 + p2}   conj(W[8 - k]).
+template <>
+struct Record<8, QSVM_FP32_SPLIT> {
+  static constexpr int kForms = 1;
+  static constexpr int kValues = 10;
+  static constexpr int kValBytes = 32;
+  static constexpr int kPartBytes = kValues * kValBytes;
+  static constexpr int kBytes = 2 * kPartBytes;
+  __host__ __device__ static constexpr int off(int v, int f, int part) { return part * kPartBytes + v * kValBytes + f * 16; }
+};
+
 __host__ __device__ constexpr size_t record_bytes(int chi, int prec) {
   return chi == 4 ? (prec == QSVM_FP64 ? 48 : prec == QSVM_FP32 ? 96 : 192)
-                  : (2 * (size_t)(chi / 2) * (chi / 2) + 1) * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1) +
-                        ((chi >= 8 && prec == QSVM_FP32_SPLIT) ? 32 : 0);
+         : (chi == 8 && prec == QSVM_FP32_SPLIT) ? 640
+                                                 : (2 * (size_t)(chi / 2) * (chi / 2) + 1) * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1);
 }
 static_assert(record_bytes(4, QSVM_FP64) == Record<4, QSVM_FP64>::kBytes, "record geometry");
 static_assert(record_bytes(4, QSVM_FP32) == Record<4, QSVM_FP32>::kBytes, "record geometry");
@@ -85,10 +100,13 @@ static_assert(record_bytes(4, QSVM_FP32_SPLIT) == Record<4, QSVM_FP32_SPLIT>::kB
 static_assert(record_bytes(2, QSVM_FP32) == Record<2, QSVM_FP32>::kBytes, "record geometry");
 static_assert(record_bytes(8, QSVM_FP32_SPLIT) == Record<8, QSVM_FP32_SPLIT>::kBytes, "record geometry");
 static_assert(record_bytes(8, QSVM_FP64) == Record<8, QSVM_FP64>::kBytes, "record geometry");
+static_assert(record_bytes(8, QSVM_FP32) == Record<8, QSVM_FP32>::kBytes, "record geometry");
 static_assert(Record<2, QSVM_FP32_SPLIT>::kBytes % 16 == 0 && Record<2, QSVM_FP64>::kBytes % 16 == 0,
               "bulk copies move whole 16-byte units");
 // arrays of records a buffer holds (the FP32 block forms keep a- and b-form arrays)
-__host__ __device__ constexpr int record_forms(int chi, int prec) { return (prec == QSVM_FP64 || chi == 4) ? 1 : 2; }
+__host__ __device__ constexpr int record_forms(int chi, int prec) {
+  return (prec == QSVM_FP64 || chi == 4 || (chi == 8 && prec == QSVM_FP32_SPLIT)) ? 1 : 2;
+}
 
 // ---- tile order --------------------------------------------------------------
 // Pair tiles are visited in bands of kBandRows tile rows; within a band column by

@@ -24,9 +24,11 @@ def test_record_and_mps_bytes():
         entries = 2 * (chi // 2) ** 2 + 1  # blocks a_00, a_01 and the phase r
         assert qsvm.qsvm_mps_record_bytes(reps, "fp64") == entries * 16
         assert qsvm.qsvm_mps_record_bytes(reps, "fp32") == entries * 16
-        pad = 32 if chi == 8 else 0  # 16 bytes after each block of the four-thread layout
-        assert qsvm.qsvm_mps_record_bytes(reps, "fp32_split") == entries * 32 + pad
+    assert qsvm.qsvm_mps_record_bytes(1, "fp32_split") == 3 * 32
     assert qsvm.qsvm_mps_bytes(64, 3, 10, "fp32") == 2 * 10 * 64 * 33 * 16
+    # split FP32 at reps = 3, phase form: nine values and r, both forms, hi and lo, one array
+    assert qsvm.qsvm_mps_record_bytes(3, "fp32_split") == 10 * 2 * 16 * 2
+    assert qsvm.qsvm_mps_bytes(64, 3, 10, "fp32_split") == 10 * 64 * 640
     # reps = 2, phase form: three phases, (re, im) doubles or both forms of 16 bytes, hi and lo
     assert qsvm.qsvm_mps_record_bytes(2, "fp64") == 48
     assert qsvm.qsvm_mps_record_bytes(2, "fp32") == 96

@@ -129,27 +129,33 @@ def test_build_mps_lowprec_formats(q):
     assert np.max(np.abs(hi + lo - f64)) <= 2 ** -34
 
 
-def test_build_mps_block_formats_reps3(q):
-    """Block-form records (reps = 3): FP64 (re, im) entries; split hi on the 2^-11 grid,
-    hi + lo within 2^-34 of FP64; the phase entry is exp(2 i theta_{k-1})."""
+def test_build_mps_formats_reps3(q):
+    """reps = 3: FP64 block records (the phase entry is exp(2 i theta_{k-1})); split FP32 in
+    phase form, W[3 ia + ib] = 2^{-3/2} P^{3 - 2 ia} T^{3 - 2 ib} and r, hi on the 2^-11 grid,
+    hi + lo within 2^-34 of the exact value, both forms."""
     N, n, reps = 3, 9, 3
     X = inputs.uniform_features(N, n, 91)
     d = _dev(X)
     f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, 33)
     theta = np.concatenate([np.zeros((N, 1)), (np.pi - X[:, :-1]) * (np.pi - X[:, 1:])], axis=1).reshape(-1)
     assert np.max(np.abs(f64[:, 32] - np.exp(2j * theta))) <= 1e-14
-    rec = q.qsvm_mps_record_bytes(reps, "fp32_split") // 4  # floats per a-form record
-    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(2, N * n, rec)
-    a = spl[0]
-    # 16-byte entries: block s starts at entry 33 s (16 hi entries, 16 lo, one unused), the phase at entry 66
-    for s in range(2):
-        for e in range(16):
-            h = a[:, 4 * (s * 33 + e):4 * (s * 33 + e) + 2]
-            lo = a[:, 4 * (s * 33 + 16 + e):4 * (s * 33 + 16 + e) + 2]
-            assert np.array_equal(np.round(h * 2048) / 2048, h)
-            h64, lo64 = h.astype(np.float64), lo.astype(np.float64)
-            v = (h64[:, 0] + lo64[:, 0]) + 1j * (h64[:, 1] + lo64[:, 1])
-            assert np.max(np.abs(v - f64[:, s * 16 + e])) <= 2 ** -30
+    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(N * n, 2, 10, 2, 4)
+    x = X.reshape(-1)
+    P, T = np.exp(-1j * x), np.exp(-1j * theta)
+    want = np.stack([2 ** -1.5 * P ** a * T ** b for a in (3, 1, -1) for b in (3, 1, -1)] + [np.exp(2j * theta)], 1)
+
+    def check_forms(a, b):  # a-form (re, im, -im, re); b-form (re, -im, im, re)
+        re, im = a[..., 0], a[..., 1]
+        assert np.array_equal(a[..., 2], -im) and np.array_equal(a[..., 3], re)
+        assert np.array_equal(b[..., 0], re) and np.array_equal(b[..., 1], -im)
+        assert np.array_equal(b[..., 2], im) and np.array_equal(b[..., 3], re)
+        return re.astype(np.float64) + 1j * im.astype(np.float64)
+
+    hi = check_forms(spl[:, 0, :, 0, :], spl[:, 0, :, 1, :])
+    lo = check_forms(spl[:, 1, :, 0, :], spl[:, 1, :, 1, :])
+    for part in (hi.real, hi.imag):
+        assert np.array_equal(np.round(part * 2048) / 2048, part)
+    assert np.max(np.abs(hi + lo - want)) <= 2 ** -34
 
 
 # ----------------------------------------------------------- small Grams ---
