@@ -7,7 +7,9 @@ m of a bond index in bit m-1, so the last layer is the HIGH bit there).
    rows with c = 1 equal the rows with c = 0 times exp(2 i theta z(sigma)).
 3. At reps = 2 every entry is +-1/2 times 1, T^2, P^2 or P^2 T^2 or a conjugate
    (P = exp(-i x_k), T = exp(-i theta_{k-1})), in the pattern the phase-form records
-   encode, and contracting with that pattern reproduces the state-vector kernel.
+   encode, and contracting with that pattern reproduces the state-vector kernel; at
+   reps = 3 every entry is +-2^{-3/2} P^A T^B or a conjugate, in the pattern of the
+   split-FP32 records at reps = 3.
 """
 import numpy as np
 import pytest
@@ -79,3 +81,26 @@ def test_reps2_phase_form_contraction(oracle):
     K = abs(E[0].sum() + E[1].sum()) ** 2
     Ko, _ = oracle.sv_kernel_pair(X[0], X[1], 2)
     assert abs(K - Ko) <= 1e-13
+
+
+def test_reps3_phase_form(oracle):
+    """At reps = 3 every entry is +-2^{-3/2} P^A T^B (A, B in {3, 1, -1}) or a conjugate:
+    with q = 2 q1 + q2, p = 2 p1 + p2 (layer 1 the high bit) and W[ia][ib] =
+    2^{-3/2} P^{3 - 2 ia} T^{3 - 2 ib}, a_00[q][p] = (-1)^{p1 p2} W[p1 + p2][(q1^p1) + (q2^p2)]
+    and a_01[q][p] = (-1)^{p1 p2 + p2} conj(W[2 - ia][2 - ib])."""
+    n = 7
+    x = inputs.uniform_features(1, n, 333)[0]
+    A = oracle.mps_closed_form(x, 3)  # oracle bit order: layer m in bit m - 1
+    th = _theta(x)
+    for k in range(1, n - 1):
+        P, T = np.exp(-1j * x[k]), np.exp(-1j * th[k])
+        W = np.array([[2 ** -1.5 * P ** a * T ** b for b in (3, 1, -1)] for a in (3, 1, -1)])
+        for s in range(2):
+            for q in range(4):
+                for p in range(4):
+                    q1, q2, p1, p2 = q >> 1, q & 1, p >> 1, p & 1
+                    val = A[k, s, q1 + 2 * q2, p1 + 2 * p2 + 4 * s]
+                    ia, ib = p1 + p2, (q1 ^ p1) + (q2 ^ p2)
+                    pred = ((-1) ** (p1 * p2) * W[ia, ib] if s == 0
+                            else (-1) ** (p1 * p2 + p2) * np.conj(W[2 - ia, 2 - ib]))
+                    assert abs(val - pred) <= 1e-14, (k, s, q, p)
