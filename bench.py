@@ -54,15 +54,16 @@ def structured_cmacs_per_entry(n: int, reps: int) -> int:
     return dense // 4
 
 
-def factorized_cmacs_per_entry(n: int, reps: int) -> int:
+def factorized_cmacs_per_entry(n: int, reps: int, prec: str = "fp64") -> int:
     """Complex MACs per kernel entry of the contraction as the kernels carry it out.
     Block form (reps 1, 3): per site rho = r(i) conj(r(j)) (1), G_s = E_0 + rho_s E_1
     (chi^2/2), X_s = a_0s^T G_s and E'_s = X_s conj(b_0s) (chi^3/4 each), bonds padded to chi.
-    Phase form (reps 2): rho (1), G (8), X and E' with the unit entries of a and b added
-    rather than multiplied (12 each): 33."""
+    Phase form (reps 2, FP64 and FP32): rho (1), G (8), X and E' with the unit entries of a
+    and b added rather than multiplied (12 each): 33.  Gauged form (reps 2, split FP32): two
+    phase products, G (8), X (8), E' (8): 26 per site over n + 1 sites (one virtual)."""
     chi = 2 ** reps
     if reps == 2:
-        return n * 33
+        return (n + 1) * 26 if prec == "fp32_split" else n * 33
     return n * (chi ** 3 // 2 + chi ** 2 // 2 + 1)
 
 
@@ -78,7 +79,7 @@ FMA_PER_CMAC = {"fp32": 4, "fp32_split": 12, "fp64": 4}
 # same configuration with the default pipeline shape (dram__bytes_read.sum +
 # dram__bytes_write.sum; profiles/pair_tile_split_n784_r2.md).  Configurations
 # not captured with the current kernel report null.
-MEASURED_TRAFFIC_BYTES = {("gram_n784_r2_N8192", "fp32_split"): 40_472_972_032 + 557_163_264}
+MEASURED_TRAFFIC_BYTES = {}
 
 
 class ClockSampler:
@@ -295,8 +296,8 @@ def run_ours(args):
         ev_mid.record(stream)
         qsvm.qsvm_kernel_gram_tiles(mps, N, n, reps, prec_code, tile_range[0], tile_range[1], K, stream=stream)
         if Nte and a1 > a0:
-            rec = qsvm.qsvm_mps_record_bytes(reps, prec_code)
-            qsvm.qsvm_kernel_cross(mps_te[a0 * n * rec:], a1 - a0, mps, N, n, reps, prec_code, K=Kx[a0:a1],
+            stride = qsvm.qsvm_mps_point_bytes(n, reps, prec_code)
+            qsvm.qsvm_kernel_cross(mps_te[a0 * stride:], a1 - a0, mps, N, n, reps, prec_code, K=Kx[a0:a1],
                                    stream=stream)
         return ev_mid
 
@@ -339,7 +340,7 @@ def run_ours(args):
     value = total_pairs / (ms * 1e-3)
 
     # ---- roofline of the dominant kernel (the pair contraction) ----
-    cm = factorized_cmacs_per_entry(n, reps)
+    cm = factorized_cmacs_per_entry(n, reps, prec)
     algo_flops = 8.0 * cm * pairs_rank
     achieved = algo_flops / (kms * 1e-3) / 1e12
     mhz = SM_MAX_MHZ_NOMINAL
@@ -518,7 +519,7 @@ def run_batch(args):
     jobs = make(P)
     ws = torch.empty(qsvm.qsvm_batch_workspace_bytes(len(jobs)), dtype=torch.uint8, device=dev)
     total_pairs = sum(j["n_points"] * (j["n_points"] + 1) // 2 for j in jobs)
-    algo_flops = sum(8.0 * factorized_cmacs_per_entry(j["n_qubits"], reps) * j["n_points"] * (j["n_points"] + 1) / 2
+    algo_flops = sum(8.0 * factorized_cmacs_per_entry(j["n_qubits"], reps, prec) * j["n_points"] * (j["n_points"] + 1) / 2
                      for j in jobs)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     build_all(jobs, P)

@@ -68,8 +68,10 @@ enum qsvm_precision {
 };
 
 /* ---- MPS storage ---------------------------------------------------------
- * One record per (point, site), point-major: record (i, k) at byte
- * (i * n_qubits + k) * qsvm_mps_record_bytes(reps, precision).  With
+ * Records per (point, site), point-major: record (i, k) of an array at byte
+ * i * qsvm_mps_point_bytes(...) + k * qsvm_mps_record_bytes(reps, precision)
+ * (k = 0 .. n_qubits - 1, and k = n_qubits for the virtual site of the gauged
+ * form).  With
  * P = exp(-i x_k), T = exp(-i theta_{k-1}), theta_{k-1} = (pi - x_{k-1})(pi - x_k)
  * (T = 1 at site 0), z(b) = 1 - 2b, right bond index u = 2p + s and left bond
  * index t = 2q + c, the site tensor is A_k[sigma][t][u] = 0 unless sigma == s
@@ -81,11 +83,20 @@ enum qsvm_precision {
  * a_01 = (1/2) [[1, -conj(P^2 T^2)], [conj(T^2), -conj(P^2)]] (rows q, columns p),
  * and the record holds the three phases V0 = T^2, V1 = P^2, V2 = P^2 T^2:
  *   QSVM_FP64        (re, im) doubles, 48 bytes;
- *   QSVM_FP32        per value its a-form then its b-form entry (below), 96 bytes;
- *   QSVM_FP32_SPLIT  the hi entries of the three values (re and im on the 2^-11
- *                    grid, both forms), then the lo entries, 192 bytes.
+ *   QSVM_FP32        per value its a-form then its b-form entry (below), 96 bytes.
  * The last site's tensor keeps its right bond open (its layer-1 spin is summed
  * by the contraction).  One array of records.
+ *
+ * Gauged form (reps = 2, QSVM_FP32_SPLIT): after the diagonal change of bond
+ * basis that makes row t = 0 of every site tensor one, both blocks of site k are
+ * [[1, 1], [alpha_k, beta_k]] with alpha_k = conj(V2^{k-1} V0^k) and
+ * beta_k = conj(V2^{k-1}) V0^k (V^k the phases of site k, V2^{-1} = 1), and
+ * a_1s = r'_s diag(1, -1) a_0s with r'_0 = alpha_k, r'_1 = beta_k.  A virtual
+ * site n with alpha_n = beta_n = conj(V2^{n-1}) undoes the basis change on the
+ * last bond.  A record holds alpha then beta, each as its hi entry (re and im on
+ * the 2^-11 grid) then its lo entry, 64 bytes; a buffer holds n_qubits + 1
+ * records per point in two arrays: the row-side a-forms, then the column-side
+ * b-forms.
  *
  * Phase form, split FP32 at reps = 3: every entry of a chi = 8 site is
  * +-2^{-3/2} P^A T^B with A, B in {3, 1, -1} (block 0) or the conjugate of one
@@ -111,9 +122,14 @@ enum qsvm_precision {
  * Forms: an a-form entry of a complex value A is (re, im, -im, re) = (A, iA);
  * a b-form entry is (re, -im, im, re) = (conj A, i conj A).  With them a complex
  * multiply-add is two packed FP32x2 FMAs with one broadcast operand.
- * qsvm_mps_bytes() is the size of a whole buffer.  The layout is private to
- * this library: produce it with qsvm_build_mps. */
+ * qsvm_mps_point_bytes() is the size of one point's records in one array (the
+ * row stride of an array): mps + m * qsvm_mps_point_bytes(...) passed as mps_a of
+ * qsvm_kernel_cross addresses the points from m on of a buffer (mps_a is read
+ * through its row-side array only).  qsvm_mps_bytes() is the size of a whole
+ * buffer; both return 0 for arguments outside their range.  The layout is
+ * private to this library: produce it with qsvm_build_mps. */
 size_t qsvm_mps_record_bytes(int32_t reps, int32_t precision);
+size_t qsvm_mps_point_bytes(int32_t n_qubits, int32_t reps, int32_t precision);
 size_t qsvm_mps_bytes(int32_t n_qubits, int32_t reps, int64_t n_points, int32_t precision);
 
 /* qsvm_build_mps -- exact MPS of U(x)|0^n> for every row of X (Sec. 3.2 circuit;
@@ -128,7 +144,8 @@ size_t qsvm_mps_bytes(int32_t n_qubits, int32_t reps, int64_t n_points, int32_t 
  * diagonal MPO that copies each spin onto the bond and applies
  * exp(-i theta Z_k Z_{k+1}), theta = (pi - x_k)(pi - x_{k+1}), on the right-hand
  * site).  reps = 2: the same gates applied to the rows t = 0, 2 (right bond open),
- * and the three phases read off three of the resulting entries.
+ * and the three phases read off three of the resulting entries (split FP32:
+ * alpha and beta formed from the phases of sites k - 1 and k).
  * Errors: QSVM_ERR_ARG (null, n_qubits < 2, n_points < 1, mps_bytes too small,
  * misaligned), QSVM_ERR_CHI (reps outside 1..3), QSVM_ERR_CUDA. */
 int32_t qsvm_build_mps(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,

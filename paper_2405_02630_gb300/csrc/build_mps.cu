@@ -121,15 +121,16 @@ __device__ __forceinline__ void site_row(int t, bool has_left, cd rz0, cd zzp, c
 // P = e^{-i x_k}, T = e^{-i theta_{k-1}} every entry is +-1/2 times one of 1,
 // T^2, P^2, P^2 T^2 or a conjugate: the record keeps those three phases, read off
 // the entries the gate-by-gate build produces.  The last site keeps the same
-// tensor with its right bond open (the contraction sums it at the end).
+// tensor with its right bond open (the contraction sums it at the end).  Split
+// FP32 stores the gauged form made from the same phases (qsvm_common.cuh).
 template <int CHI, int PREC>
 __device__ __forceinline__ void store_phase(uint8_t* rec, int v, cd z) {
   using Rec = Record<CHI, PREC>;
-  if constexpr (PREC == QSVM_FP64) {
-    reinterpret_cast<double2*>(rec + Rec::off(v, 0, 0))[0] = make_double2(z.re, z.im);
-  } else if constexpr (PREC == QSVM_FP32) {
-    store_forms(rec + Rec::off(v, 0, 0), rec + Rec::off(v, 1, 0), __double2float_rn(z.re), __double2float_rn(z.im));
-  } else {
+  if constexpr (PREC == QSVM_FP64) {  // reps = 2
+    reinterpret_cast<double2*>(rec + Rec::off(v, 0))[0] = make_double2(z.re, z.im);
+  } else if constexpr (PREC == QSVM_FP32) {  // reps = 2
+    store_forms(rec + Rec::off(v, 0), rec + Rec::off(v, 1), __double2float_rn(z.re), __double2float_rn(z.im));
+  } else {  // split FP32, reps = 3
     constexpr double sc = (double)(1 << kGridT);
     const double hr = rint(z.re * sc) / sc, hi = rint(z.im * sc) / sc;
     store_forms(rec + Rec::off(v, 0, 0), rec + Rec::off(v, 1, 0), (float)hr, (float)hi);
@@ -137,6 +138,63 @@ __device__ __forceinline__ void store_phase(uint8_t* rec, int v, cd z) {
                 __double2float_rn(z.im - hi));
   }
 }
+
+// Gauged-form record (split FP32, reps = 2) of site k of point i: alpha and beta,
+// hi on 2^-kGridT and the lo remainder, a-form entries into the row-side array and
+// b-form entries into the column-side array (n + 1 records per point each).
+__device__ __forceinline__ void store_gauged(uint8_t* mps, int64_t n_points, int n, int64_t i, int k, cd alpha,
+                                             cd beta) {
+  using Rec = Record<4, QSVM_FP32_SPLIT>;
+  const int64_t sites = record_sites(n, 4, QSVM_FP32_SPLIT);
+  uint8_t* pa = mps + (i * sites + k) * Rec::kBytes;
+  uint8_t* pb = pa + n_points * sites * Rec::kBytes;
+  constexpr double sc = (double)(1 << kGridT);
+  const cd z[2] = {alpha, beta};
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    const double hr = rint(z[v].re * sc) / sc, hi = rint(z[v].im * sc) / sc;
+    store_forms(pa + Rec::off(v, 0), pb + Rec::off(v, 0), (float)hr, (float)hi);
+    store_forms(pa + Rec::off(v, 1), pb + Rec::off(v, 1), __double2float_rn(z[v].re - hr),
+                __double2float_rn(z[v].im - hi));
+  }
+}
+
+// The gate parameters of site k of point i: rz0 = e^{-i x_k}; zzp, zzm = exp(-+i theta_{k-1}).
+__device__ __forceinline__ void site_params(const double* X, int64_t i, int n, int k, cd& rz0, cd& zzp, cd& zzm) {
+  const double xk = X[i * n + k];
+  double sx, cx;
+  sincos(xk, &sx, &cx);
+  rz0 = cd{cx, -sx};
+  zzp = zzm = cd{1.0, 0.0};
+  if (k > 0) {
+    const double th = (kPi - X[i * n + k - 1]) * (kPi - xk);
+    double st, ct;
+    sincos(th, &st, &ct);
+    zzp = cd{ct, -st};  // a = 0: z(a) = +1 -> exp(-i theta) for sigma = 0
+    zzm = cd{ct, st};   // a = 1: z(a) = -1 -> exp(+i theta) for sigma = 0
+  }
+}
+
+// The three phases V0 = T^2, V1 = P^2, V2 = P^2 T^2 of site k (reps = 2), read off
+// rows t = 0 and t = 2 of the gate-by-gate build (right bond open, also at the last
+// site): a_00[0][0] = V2 / 2, a_00[1][0] = V1 / 2, a_00[1][1] = V0 / 2.  Site 0 has
+// only t = 0; there T = 1, so V0 = 1 and V1 = V2.
+__device__ __forceinline__ void phases_r2(const double* X, int64_t i, int n, int k, cd& V0, cd& V1, cd& V2) {
+  cd rz0, zzp, zzm;
+  site_params(X, i, n, k, rz0, zzp, zzm);
+  cd v[2][4];
+  site_row<2, false>(0, k > 0, rz0, zzp, zzm, v);
+  V2 = cd{2.0 * v[0][0].re, 2.0 * v[0][0].im};
+  V1 = V2;
+  V0 = cd{1.0, 0.0};
+  if (k > 0) {
+    site_row<2, false>(2, true, rz0, zzp, zzm, v);
+    V1 = cd{2.0 * v[0][0].re, 2.0 * v[0][0].im};
+    V0 = cd{2.0 * v[0][2].re, 2.0 * v[0][2].im};
+  }
+}
+
+__device__ __forceinline__ cd conj_(cd a) { return cd{a.re, -a.im}; }
 
 template <int R, int PREC>
 __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict__ X, int64_t n_points, int n,
@@ -147,33 +205,21 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
   if (gid >= n_points * (int64_t)n) return;
   const int64_t i = gid / n;
   const int k = (int)(gid - i * n);
-  const double xk = X[i * n + k];
-  double sx, cx;
-  sincos(xk, &sx, &cx);
-  const cd rz0 = cd{cx, -sx};  // e^{-i x_k}
-  cd zzp = cd{1.0, 0.0}, zzm = cd{1.0, 0.0};
+  cd rz0, zzp, zzm;
+  site_params(X, i, n, k, rz0, zzp, zzm);
   const bool has_left = k > 0;
-  if (has_left) {
-    const double th = (kPi - X[i * n + k - 1]) * (kPi - xk);
-    double st, ct;
-    sincos(th, &st, &ct);
-    zzp = cd{ct, -st};  // a = 0: z(a) = +1 -> exp(-i theta) for sigma = 0
-    zzm = cd{ct, st};   // a = 1: z(a) = -1 -> exp(+i theta) for sigma = 0
-  }
-  if constexpr (R == 2) {
-    // Apply the site's gates to rows t = 0 and t = 2 (right bond open, also at the
-    // last site) and read the three phases off the entries a_00[0][0] = V2 / 2,
-    // a_00[1][0] = V1 / 2, a_00[1][1] = V0 / 2.  Site 0 has only t = 0; there
-    // T = 1, so V0 = 1 and V1 = V2.
-    cd v[2][CHI];
-    site_row<R, false>(0, has_left, rz0, zzp, zzm, v);
-    const cd V2 = cd{2.0 * v[0][0].re, 2.0 * v[0][0].im};
-    cd V1 = V2, V0 = cd{1.0, 0.0};
-    if (has_left) {
-      site_row<R, false>(2, has_left, rz0, zzp, zzm, v);
-      V1 = cd{2.0 * v[0][0].re, 2.0 * v[0][0].im};
-      V0 = cd{2.0 * v[0][2].re, 2.0 * v[0][2].im};
-    }
+  if constexpr (R == 2 && PREC == QSVM_FP32_SPLIT) {
+    // gauged form: alpha_k = conj(V2^{k-1} V0^k), beta_k = conj(V2^{k-1}) V0^k
+    // (V2^{-1} = 1); the thread of the last site also writes the virtual site n
+    cd V0, V1, V2, P0, P1, V2p = cd{1.0, 0.0};
+    phases_r2(X, i, n, k, V0, V1, V2);
+    if (has_left) phases_r2(X, i, n, k - 1, P0, P1, V2p);
+    const cd c = conj_(V2p);
+    store_gauged(mps, n_points, n, i, k, cmul(c, conj_(V0)), cmul(c, V0));
+    if (k == n - 1) store_gauged(mps, n_points, n, i, n, conj_(V2), conj_(V2));
+  } else if constexpr (R == 2) {
+    cd V0, V1, V2;
+    phases_r2(X, i, n, k, V0, V1, V2);
     uint8_t* rec = mps + gid * Record<4, PREC>::kBytes;
     store_phase<4, PREC>(rec, 0, V0);
     store_phase<4, PREC>(rec, 1, V1);

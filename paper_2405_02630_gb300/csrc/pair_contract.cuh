@@ -322,11 +322,11 @@ struct Engine<CHI, QSVM_FP32> {
 // else is rounded.  This is the split hi+lo compensated product carried out on
 // the FP32 pipe: 6 packed FMAs (12 FMAs) per complex MAC.
 
-// u conj(w) for split values given as u's a-form entries (hi at ah, lo at al) and
-// w's b-form entries (hi at bh, lo at bl), returned as the split forms of both
-// rho_0 = u conj(w) and rho_1 = conj(rho_0): R[s] = rho_s, iR[s] = i rho_s.
-__device__ __forceinline__ void split_phase(uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl, float2 (&Rh)[2],
-                                            float2 (&iRh)[2], float2 (&Rl)[2], float2 (&iRl)[2]) {
+// rho = u conj(w) for split values given as u's a-form entries (hi at ah, lo at al)
+// and w's b-form entries (hi at bh, lo at bl), returned as the split forms R = rho,
+// iR = i rho; hi(rho) on 2^-kGridT.
+__device__ __forceinline__ void split_rho(uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl, float2& Rh, float2& iRh,
+                                          float2& Rl, float2& iRl) {
   const float4 ih = *reinterpret_cast<const float4*>(sptr(ah));
   const float4 il = *reinterpret_cast<const float4*>(sptr(al));
   const float4 jh = *reinterpret_cast<const float4*>(sptr(bh));
@@ -339,14 +339,20 @@ __device__ __forceinline__ void split_phase(uint32_t ah, uint32_t al, uint32_t b
   const float2 v = add2(h, l);
   const float2 rh = grid_round2<kGridT>(v);
   const float2 rl = add2(fma2(rh, make_float2(-1.f, -1.f), h), l);  // (h - rh) is exact
-  Rh[0] = rh;
-  iRh[0] = make_float2(-rh.y, rh.x);
-  Rh[1] = make_float2(rh.x, -rh.y);
-  iRh[1] = make_float2(rh.y, rh.x);
-  Rl[0] = rl;
-  iRl[0] = make_float2(-rl.y, rl.x);
-  Rl[1] = make_float2(rl.x, -rl.y);
-  iRl[1] = make_float2(rl.y, rl.x);
+  Rh = rh;
+  iRh = make_float2(-rh.y, rh.x);
+  Rl = rl;
+  iRl = make_float2(-rl.y, rl.x);
+}
+
+// As split_rho, also returning the forms of rho_1 = conj(rho_0): R[s] = rho_s, iR[s] = i rho_s.
+__device__ __forceinline__ void split_phase(uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl, float2 (&Rh)[2],
+                                            float2 (&iRh)[2], float2 (&Rl)[2], float2 (&iRl)[2]) {
+  split_rho(ah, al, bh, bl, Rh[0], iRh[0], Rl[0], iRl[0]);
+  Rh[1] = make_float2(Rh[0].x, -Rh[0].y);
+  iRh[1] = make_float2(Rh[0].y, Rh[0].x);
+  Rl[1] = make_float2(Rl[0].x, -Rl[0].y);
+  iRl[1] = make_float2(Rl[0].y, Rl[0].x);
 }
 
 // G = E_0 + rho E_1 split onto the 2^-GG grid (hi, lo, full).
@@ -633,10 +639,9 @@ struct Engine<4, QSVM_FP64> {
   }
 };
 
-// Form pair (V, iV) (f = 0) or (conj V, i conj V) (f = 1) of phase v of a record.
-template <int PREC>
-__device__ __forceinline__ void phase_form(uint32_t rec, int v, int f, int part, float2& x, float2& ix) {
-  const float4 q = *reinterpret_cast<const float4*>(sptr(rec + Record<4, PREC>::off(v, f, part)));
+// Form pair (V, iV) (f = 0) or (conj V, i conj V) (f = 1) of phase v of an FP32 record.
+__device__ __forceinline__ void phase_form(uint32_t rec, int v, int f, float2& x, float2& ix) {
+  const float4 q = *reinterpret_cast<const float4*>(sptr(rec + Record<4, QSVM_FP32>::off(v, f)));
   x = make_float2(q.x, q.y);
   ix = make_float2(q.z, q.w);
 }
@@ -668,8 +673,8 @@ struct Engine<4, QSVM_FP32> {
     const float2 z = make_float2(0.f, 0.f);
     float2 x0, ix0, x1, ix1, x2, ix2;
     // rho_0 = W0 conj(V0)
-    phase_form<QSVM_FP32>(rb, 0, 0, 0, x0, ix0);
-    phase_form<QSVM_FP32>(ra, 0, 1, 0, x1, ix1);
+    phase_form(rb, 0, 0, x0, ix0);
+    phase_form(ra, 0, 1, x1, ix1);
     const float2 r0 = cmac(x0, x1, ix1, z);
     const float2 R0 = r0, iR0 = make_float2(-r0.y, r0.x), R1 = make_float2(r0.x, -r0.y), iR1 = make_float2(r0.y, r0.x);
 #pragma unroll
@@ -682,34 +687,34 @@ struct Engine<4, QSVM_FP32> {
       }
     float2 X[2][2];
     // s = 0: row phases in a-form, column phases in b-form
-    phase_form<QSVM_FP32>(ra, 0, 0, 0, x0, ix0);
-    phase_form<QSVM_FP32>(ra, 1, 0, 0, x1, ix1);
-    phase_form<QSVM_FP32>(ra, 2, 0, 0, x2, ix2);
+    phase_form(ra, 0, 0, x0, ix0);
+    phase_form(ra, 1, 0, x1, ix1);
+    phase_form(ra, 2, 0, x2, ix2);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       X[0][r] = cmac(E[0][1][r], x1, ix1, cmac(E[0][0][r], x2, ix2, z));
       X[1][r] = cmac(E[0][1][r], x0, ix0, E[0][0][r]);
     }
-    phase_form<QSVM_FP32>(rb, 0, 1, 0, x0, ix0);
-    phase_form<QSVM_FP32>(rb, 1, 1, 0, x1, ix1);
-    phase_form<QSVM_FP32>(rb, 2, 1, 0, x2, ix2);
+    phase_form(rb, 0, 1, x0, ix0);
+    phase_form(rb, 1, 1, x1, ix1);
+    phase_form(rb, 2, 1, x2, ix2);
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       E[0][p][0] = cmac(X[p][1], x1, ix1, cmac(X[p][0], x2, ix2, z));
       E[0][p][1] = cmac(X[p][1], x0, ix0, X[p][0]);
     }
     // s = 1: row phases in b-form, column phases in a-form
-    phase_form<QSVM_FP32>(ra, 0, 1, 0, x0, ix0);
-    phase_form<QSVM_FP32>(ra, 1, 1, 0, x1, ix1);
-    phase_form<QSVM_FP32>(ra, 2, 1, 0, x2, ix2);
+    phase_form(ra, 0, 1, x0, ix0);
+    phase_form(ra, 1, 1, x1, ix1);
+    phase_form(ra, 2, 1, x2, ix2);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       X[0][r] = cmac(E[1][1][r], x0, ix0, E[1][0][r]);
       X[1][r] = cmac(E[1][1][r], x1, ix1, cmac(E[1][0][r], x2, ix2, z));  // X~[1][r]
     }
-    phase_form<QSVM_FP32>(rb, 0, 0, 0, x0, ix0);
-    phase_form<QSVM_FP32>(rb, 1, 0, 0, x1, ix1);
-    phase_form<QSVM_FP32>(rb, 2, 0, 0, x2, ix2);
+    phase_form(rb, 0, 0, x0, ix0);
+    phase_form(rb, 1, 0, x1, ix1);
+    phase_form(rb, 2, 0, x2, ix2);
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       const float2 n0 = cmac(X[p][1], x0, ix0, X[p][0]);
@@ -771,7 +776,19 @@ struct SplitForm {
 
 template <>
 struct Engine<4, QSVM_FP32_SPLIT> {
-  static constexpr int GG = 9, GX = 8;
+  // Gauged form: both blocks of a site are [[1, 1], [alpha, beta]] (row point) and
+  // conj of the column point's, block c = 1 adds the factor r'_s S (S = diag(1, -1)).
+  // Per site and s: G_s = E_0 + rho_s E_1 with rho_0 = alpha_i conj(alpha_j) and
+  // rho_1 = beta_i conj(beta_j) (E_1 is stored with the signs of S E_1 S applied);
+  // X_s[p][r] = G_s[0][r] + a[p] G_s[1][r] (a = (alpha_i, beta_i)); E'_s[p][pp] =
+  // X_s[p][0] + X_s[p][1] conj(b[pp]) (b = (alpha_j, beta_j)): 24 complex MACs and
+  // two phase products per site.  Grids: hi(rho) on 2^-kGridT, hi(E) on 2^-kGridE,
+  // hi(G) on 2^-GG, hi(X) on 2^-GX.  Exactness (|hi(alpha)|, |hi(rho)| <= 1.0004,
+  // E's components <= 1): hi(G) sums on 2^-21 with partial sums <= 3 (< 2^23 units);
+  // |G| <= 2.83, so hi(X) sums on 2^-(GG + kGridT) = 2^-21 stay below 5.67 < 8
+  // (< 2^24 units); |X| <= 5.67, so hi(E') sums on 2^-(GX + kGridT) = 2^-20 stay
+  // below 11.4 < 16.
+  static constexpr int GG = kGridG, GX = 9;
   static constexpr int kRenormEvery = 1;  // built into site()
   using Rec = Record<4, QSVM_FP32_SPLIT>;
   float2 Eh[2][2][2], El[2][2][2], Ef[2][2][2];  // Ef = fl(Eh + El)
@@ -785,13 +802,18 @@ struct Engine<4, QSVM_FP32_SPLIT> {
 #pragma unroll
         for (int r = 0; r < 2; ++r) Eh[c][q][r] = El[c][q][r] = Ef[c][q][r] = make_float2(0.f, 0.f);
     Eh[0][0][0].x = Ef[0][0][0].x = 1.f;
-    L = 0;
+    L = 2;  // every site() counts -2 for the factors 1/2 of a and b; the virtual site has none
   }
 
-  static __device__ __forceinline__ SplitForm form(uint32_t rec, int v, int f) {
+  // split forms of value v of a record (a-form array: (V, iV); b-form array: (conj V, i conj V))
+  static __device__ __forceinline__ SplitForm form(uint32_t rec, int v) {
     SplitForm F;
-    phase_form<QSVM_FP32_SPLIT>(rec, v, f, 0, F.h, F.ih);
-    phase_form<QSVM_FP32_SPLIT>(rec, v, f, 1, F.l, F.il);
+    const float4 qh = *reinterpret_cast<const float4*>(sptr(rec + Rec::off(v, 0)));
+    const float4 ql = *reinterpret_cast<const float4*>(sptr(rec + Rec::off(v, 1)));
+    F.h = make_float2(qh.x, qh.y);
+    F.ih = make_float2(qh.z, qh.w);
+    F.l = make_float2(ql.x, ql.y);
+    F.il = make_float2(ql.z, ql.w);
     return F;
   }
   // (hh, ll) += w V for a split w (hi, lo, full) and a split form of V
@@ -804,20 +826,21 @@ struct Engine<4, QSVM_FP32_SPLIT> {
     ll = fma2(bc(wf.x), V.l, ll);
     ll = fma2(bc(wf.y), V.il, ll);
   }
-  template <int GR>
+  template <int GS>
   static __device__ __forceinline__ void ssplit(float2 hh, float2 ll, float2& xh, float2& xl, float2& xf) {
     const float2 v = add2(hh, ll);
-    xh = grid_round2<GR>(v);
+    xh = grid_round2<GS>(v);
     xl = add2(fma2(xh, make_float2(-1.f, -1.f), hh), ll);  // (hh - xh) is exact
     xf = v;
   }
 
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
-    const float2 z = make_float2(0.f, 0.f);
     float2 Rh[2], iRh[2], Rl[2], iRl[2];
-    // rho_0 = W0 conj(V0): W0's a-form entries and V0's b-form entries
-    split_phase(rb + Rec::off(0, 0, 0), rb + Rec::off(0, 0, 1), ra + Rec::off(0, 1, 0), ra + Rec::off(0, 1, 1), Rh, iRh,
-                Rl, iRl);
+    split_rho(ra + Rec::off(0, 0), ra + Rec::off(0, 1), rb + Rec::off(0, 0), rb + Rec::off(0, 1), Rh[0], iRh[0], Rl[0],
+              iRl[0]);
+    split_rho(ra + Rec::off(1, 0), ra + Rec::off(1, 1), rb + Rec::off(1, 0), rb + Rec::off(1, 1), Rh[1], iRh[1], Rl[1],
+              iRl[1]);
+    // G_s = E_0 + rho_s E_1 in place of E_s
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -829,65 +852,31 @@ struct Engine<4, QSVM_FP32_SPLIT> {
           split_mix<GG>(e0h, e0l, e1h, e1l, e1f, Rh[s], iRh[s], Rl[s], iRl[s], Eh[s][q][r], El[s][q][r],
                         Ef[s][q][r]);
       }
+    const SplitForm A0 = form(ra, 0), A1 = form(ra, 1);
+    const SplitForm B0 = form(rb, 0), B1 = form(rb, 1);
     float2 Nh[2][2][2], Nl[2][2][2];
-    float2 Xh[2][2], Xl[2][2], Xf[2][2];
-    {  // s = 0
-      const SplitForm V0 = form(ra, 0, 0), V1 = form(ra, 1, 0), V2 = form(ra, 2, 0);
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        float2 hh = z, ll = z;
-        smac(hh, ll, Eh[0][0][r], El[0][0][r], Ef[0][0][r], V2);
-        smac(hh, ll, Eh[0][1][r], El[0][1][r], Ef[0][1][r], V1);
-        ssplit<GX>(hh, ll, Xh[0][r], Xl[0][r], Xf[0][r]);
-        hh = Eh[0][0][r];
-        ll = El[0][0][r];
-        smac(hh, ll, Eh[0][1][r], El[0][1][r], Ef[0][1][r], V0);
-        ssplit<GX>(hh, ll, Xh[1][r], Xl[1][r], Xf[1][r]);
-      }
-      const SplitForm W0 = form(rb, 0, 1), W1 = form(rb, 1, 1), W2 = form(rb, 2, 1);
+    for (int s = 0; s < 2; ++s) {
+      float2 Xh[2][2], Xl[2][2], Xf[2][2];
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        float2 hh = z, ll = z;
-        smac(hh, ll, Xh[p][0], Xl[p][0], Xf[p][0], W2);
-        smac(hh, ll, Xh[p][1], Xl[p][1], Xf[p][1], W1);
-        Nh[0][p][0] = hh;
-        Nl[0][p][0] = ll;
-        hh = Xh[p][0];
-        ll = Xl[p][0];
-        smac(hh, ll, Xh[p][1], Xl[p][1], Xf[p][1], W0);
-        Nh[0][p][1] = hh;
-        Nl[0][p][1] = ll;
-      }
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          float2 hh = Eh[s][0][r], ll = El[s][0][r];
+          smac(hh, ll, Eh[s][1][r], El[s][1][r], Ef[s][1][r], p ? A1 : A0);
+          ssplit<GX>(hh, ll, Xh[p][r], Xl[p][r], Xf[p][r]);
+        }
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp) {
+          float2 hh = Xh[p][0], ll = Xl[p][0];
+          smac(hh, ll, Xh[p][1], Xl[p][1], Xf[p][1], pp ? B1 : B0);
+          Nh[s][p][pp] = hh;
+          Nl[s][p][pp] = ll;
+        }
     }
-    {  // s = 1 (row 1 of X holds X~; the signs are applied below)
-      const SplitForm V0 = form(ra, 0, 1), V1 = form(ra, 1, 1), V2 = form(ra, 2, 1);
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        float2 hh = Eh[1][0][r], ll = El[1][0][r];
-        smac(hh, ll, Eh[1][1][r], El[1][1][r], Ef[1][1][r], V0);
-        ssplit<GX>(hh, ll, Xh[0][r], Xl[0][r], Xf[0][r]);
-        hh = z;
-        ll = z;
-        smac(hh, ll, Eh[1][0][r], El[1][0][r], Ef[1][0][r], V2);
-        smac(hh, ll, Eh[1][1][r], El[1][1][r], Ef[1][1][r], V1);
-        ssplit<GX>(hh, ll, Xh[1][r], Xl[1][r], Xf[1][r]);
-      }
-      const SplitForm W0 = form(rb, 0, 0), W1 = form(rb, 1, 0), W2 = form(rb, 2, 0);
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        float2 hh = Xh[p][0], ll = Xl[p][0];
-        smac(hh, ll, Xh[p][1], Xl[p][1], Xf[p][1], W0);
-        Nh[1][p][0] = hh;
-        Nl[1][p][0] = ll;
-        hh = z;
-        ll = z;
-        smac(hh, ll, Xh[p][0], Xl[p][0], Xf[p][0], W2);
-        smac(hh, ll, Xh[p][1], Xl[p][1], Xf[p][1], W1);
-        Nh[1][p][1] = hh;
-        Nl[1][p][1] = ll;
-      }
-    }
-    // renormalise by 2^-e, apply the signs (-1)^{p+pp} of block 1, re-split onto the E grid
+    // renormalise by 2^-e, apply the signs (-1)^{p+pp} of S E_1 S, re-split onto the E grid
     const float2 m1 = make_float2(-1.f, -1.f);
     float2 V[2][2][2];
 #pragma unroll
@@ -935,18 +924,10 @@ struct Engine<4, QSVM_FP32_SPLIT> {
 
   __device__ __forceinline__ void renorm() {}
 
+  // after the virtual site the amplitude is entry (0, 0) of block 0 (up to a phase)
   __device__ __forceinline__ void amplitude(double& re, double& im) const {
-    re = 0.0;
-    im = 0.0;
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          re = __dadd_rn(re, __dadd_rn((double)Eh[s][p][r].x, (double)El[s][p][r].x));
-          im = __dadd_rn(im, __dadd_rn((double)Eh[s][p][r].y, (double)El[s][p][r].y));
-        }
+    re = __dadd_rn((double)Eh[0][0][0].x, (double)El[0][0][0].x);
+    im = __dadd_rn((double)Eh[0][0][0].y, (double)El[0][0][0].y);
   }
 };
 
@@ -1265,7 +1246,7 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
   const int64_t i0 = w.ti * TI, j0 = w.tj * TI;
   const int ni = (int)((w.nA - i0) < TI ? (w.nA - i0) : TI);
   const int nj = (int)((w.nB - j0) < TI ? (w.nB - j0) : TI);
-  const int n = w.n;
+  const int n = record_sites(w.n, CHI, PREC);  // records per point (sites, plus a virtual one)
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int pair = tid / TPP, quarter = tid % TPP;
@@ -1483,7 +1464,9 @@ __global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>())
     TileWork w;
     sym_tile_decode(t - args.prefix[lo], J.tiles, w.ti, w.tj);
     w.mpsA = J.mps;
-    w.mpsB = J.mps + (Record<CHI, PREC>::kForms == 2 ? J.n_points * (int64_t)J.n_qubits * Record<CHI, PREC>::kBytes : 0);
+    w.mpsB = J.mps + (Record<CHI, PREC>::kForms == 2
+                          ? J.n_points * (int64_t)record_sites(J.n_qubits, CHI, PREC) * Record<CHI, PREC>::kBytes
+                          : 0);
     w.nA = w.nB = J.n_points;
     w.n = J.n_qubits;
     w.symmetric = 1;

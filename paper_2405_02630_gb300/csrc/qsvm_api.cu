@@ -72,7 +72,10 @@ int64_t tiles_per_side(int64_t n_points, int tdim) { return (n_points + tdim - 1
 
 // byte offset of the column-side (b-form) records inside an MPS buffer
 size_t form_b_offset(int64_t n_points, int n_qubits, int reps, int prec) {
-  return record_forms(1 << reps, prec) == 2 ? record_bytes(1 << reps, prec) * (size_t)n_points * (size_t)n_qubits : 0;
+  const int chi = 1 << reps;
+  return record_forms(chi, prec) == 2
+             ? record_bytes(chi, prec) * (size_t)n_points * (size_t)record_sites(n_qubits, chi, prec)
+             : 0;
 }
 
 // selected pipeline configuration per (reps - 1, precision); -1 = default
@@ -208,9 +211,15 @@ size_t qsvm_mps_record_bytes(int32_t reps, int32_t precision) {
   return record_bytes(1 << reps, precision);
 }
 
+size_t qsvm_mps_point_bytes(int32_t n_qubits, int32_t reps, int32_t precision) {
+  if (n_qubits < 1) return 0;
+  const size_t rec = qsvm_mps_record_bytes(reps, precision);
+  return rec ? rec * (size_t)record_sites(n_qubits, 1 << reps, precision) : 0;
+}
+
 size_t qsvm_mps_bytes(int32_t n_qubits, int32_t reps, int64_t n_points, int32_t precision) {
   if (n_qubits < 1 || n_points < 0) return 0;
-  return qsvm_mps_record_bytes(reps, precision) * (size_t)record_forms(1 << reps, precision) * (size_t)n_qubits *
+  return qsvm_mps_point_bytes(n_qubits, reps, precision) * (size_t)record_forms(1 << reps, precision) *
          (size_t)n_points;
 }
 

@@ -57,18 +57,37 @@ struct Record {
 // and r = conj(T^2).  A record holds the three unit phases V_0 = T^2, V_1 = P^2,
 // V_2 = P^2 T^2 (the factors 1/2 are carried in the log scale).  FP64: (re, im)
 // doubles.  FP32: per value its a-form then its b-form entry (each side of a
-// pair needs both), one array.  Split FP32: the hi entries of the three values
-// (both forms), then the lo entries.
+// pair needs both), one array.  (Split FP32 uses the gauged form below.)
 template <int PREC>
 struct Record<4, PREC> {
   static constexpr int H = 2;
   static constexpr int kForms = 1;
-  static constexpr int kParts = (PREC == QSVM_FP32_SPLIT) ? 2 : 1;
-  static constexpr int kValBytes = (PREC == QSVM_FP64) ? 16 : 32;  // one value, all its forms, one part
-  static constexpr int kPartBytes = 3 * kValBytes;
-  static constexpr int kBytes = kParts * kPartBytes;
-  // byte offset of value v (0: T^2, 1: P^2, 2: P^2 T^2), form f (0: a, 1: b), part (0: hi, 1: lo)
-  __host__ __device__ static constexpr int off(int v, int f, int part) { return part * kPartBytes + v * kValBytes + f * 16; }
+  static constexpr int kValBytes = (PREC == QSVM_FP64) ? 16 : 32;  // one value, all its forms
+  static constexpr int kBytes = 3 * kValBytes;
+  // byte offset of value v (0: T^2, 1: P^2, 2: P^2 T^2), form f (0: a, 1: b)
+  __host__ __device__ static constexpr int off(int v, int f) { return v * kValBytes + f * 16; }
+};
+
+// Gauged form (split FP32, reps = 2).  A diagonal change of basis on every bond
+// leaves the state unchanged; the one that makes the first row (t = 0) of every
+// site tensor equal to one turns both blocks of site k into the same matrix
+//     a_0s = [[1, 1], [alpha_k, beta_k]],   alpha_k = conj(V_2^{k-1} V_0^k),
+//     beta_k = conj(V_2^{k-1}) V_0^k        (V^{k} the phases of site k above),
+// with a_1s = r'_s S a_0s, S = diag(1, -1), r'_0 = alpha_k and r'_1 = beta_k
+// (and unit-modulus entries: the factors 1/2 stay in the log scale).  The basis
+// change left on the last bond is undone by one more, virtual site n with
+// alpha_n = beta_n = conj(V_2^{n-1}); the amplitude is then entry (0, 0) of
+// block 0 of the environment after site n, up to a phase.  Site 0 (left bond 1)
+// stores alpha_0 = beta_0 = 1.  A record holds alpha then beta, each as its hi
+// entry then its lo entry; the buffer keeps n + 1 records per point, an a-form
+// array (row side) and then a b-form array (column side), so each side of a pair
+// reads 64 bytes per site.
+template <>
+struct Record<4, QSVM_FP32_SPLIT> {
+  static constexpr int kForms = 2;
+  static constexpr int kBytes = 64;
+  // byte offset of value v (0: alpha, 1: beta), part (0: hi, 1: lo) within one form's record
+  __host__ __device__ static constexpr int off(int v, int part) { return v * 32 + part * 16; }
 };
 
 // Phase form for split FP32 at reps = 3.  Every entry of a chi = 8 site is
@@ -90,7 +109,7 @@ struct Record<8, QSVM_FP32_SPLIT> {
 };
 
 __host__ __device__ constexpr size_t record_bytes(int chi, int prec) {
-  return chi == 4 ? (prec == QSVM_FP64 ? 48 : prec == QSVM_FP32 ? 96 : 192)
+  return chi == 4 ? (prec == QSVM_FP64 ? 48 : prec == QSVM_FP32 ? 96 : 64)
          : (chi == 8 && prec == QSVM_FP32_SPLIT) ? 640
                                                  : (2 * (size_t)(chi / 2) * (chi / 2) + 1) * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1);
 }
@@ -103,9 +122,14 @@ static_assert(record_bytes(8, QSVM_FP64) == Record<8, QSVM_FP64>::kBytes, "recor
 static_assert(record_bytes(8, QSVM_FP32) == Record<8, QSVM_FP32>::kBytes, "record geometry");
 static_assert(Record<2, QSVM_FP32_SPLIT>::kBytes % 16 == 0 && Record<2, QSVM_FP64>::kBytes % 16 == 0,
               "bulk copies move whole 16-byte units");
-// arrays of records a buffer holds (the FP32 block forms keep a- and b-form arrays)
+// arrays of records a buffer holds (the FP32 block forms and the gauged form keep
+// a- and b-form arrays)
 __host__ __device__ constexpr int record_forms(int chi, int prec) {
-  return (prec == QSVM_FP64 || chi == 4 || (chi == 8 && prec == QSVM_FP32_SPLIT)) ? 1 : 2;
+  return (prec == QSVM_FP64 || (chi == 4 && prec == QSVM_FP32) || (chi == 8 && prec == QSVM_FP32_SPLIT)) ? 1 : 2;
+}
+// records per point and array: one per site, plus the virtual site of the gauged form
+__host__ __device__ constexpr int record_sites(int n_qubits, int chi, int prec) {
+  return n_qubits + ((chi == 4 && prec == QSVM_FP32_SPLIT) ? 1 : 0);
 }
 
 // ---- tile order --------------------------------------------------------------

@@ -55,6 +55,7 @@ class QsvmSvcProblem(ctypes.Structure):
 
 _SIGS = {
     "qsvm_mps_record_bytes": (_sz, [_i32, _i32]),
+    "qsvm_mps_point_bytes": (_sz, [_i32, _i32, _i32]),
     "qsvm_mps_bytes": (_sz, [_i32, _i32, _i64, _i32]),
     "qsvm_build_mps": (_i32, [_dp, _i64, _i32, _i32, _i32, _vp, _sz, _vp]),
     "qsvm_kernel_gram": (_i32, [_vp, _i64, _i32, _i32, _i32, _dp, _i64, _dp, _i64, _vp]),
@@ -138,6 +139,10 @@ def _ptr(t):
 # ---------------------------------------------------------------- queries ---
 def qsvm_mps_record_bytes(reps: int, precision) -> int:
     return int(lib().qsvm_mps_record_bytes(reps, _prec(precision)))
+
+
+def qsvm_mps_point_bytes(n_qubits: int, reps: int, precision) -> int:
+    return int(lib().qsvm_mps_point_bytes(n_qubits, reps, _prec(precision)))
 
 
 def qsvm_mps_bytes(n_qubits: int, reps: int, n_points: int, precision) -> int:

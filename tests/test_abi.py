@@ -29,13 +29,21 @@ def test_record_and_mps_bytes():
     # split FP32 at reps = 3, phase form: nine values and r, both forms, hi and lo, one array
     assert qsvm.qsvm_mps_record_bytes(3, "fp32_split") == 10 * 2 * 16 * 2
     assert qsvm.qsvm_mps_bytes(64, 3, 10, "fp32_split") == 10 * 64 * 640
-    # reps = 2, phase form: three phases, (re, im) doubles or both forms of 16 bytes, hi and lo
+    # reps = 2, phase form: three phases, (re, im) doubles or both forms of 16 bytes
     assert qsvm.qsvm_mps_record_bytes(2, "fp64") == 48
     assert qsvm.qsvm_mps_record_bytes(2, "fp32") == 96
-    assert qsvm.qsvm_mps_record_bytes(2, "fp32_split") == 192
     assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp64") == 8192 * 784 * 48
     assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32") == 8192 * 784 * 96
-    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 8192 * 784 * 192
+    # reps = 2, split FP32, gauged form: alpha and beta, hi and lo, per form; n + 1 records
+    # (one virtual site) per point in a row-side and a column-side array
+    assert qsvm.qsvm_mps_record_bytes(2, "fp32_split") == 64
+    assert qsvm.qsvm_mps_point_bytes(784, 2, "fp32_split") == 785 * 64
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 2 * 8192 * 785 * 64
+    # the row stride of one array: sites x record bytes (block form: two arrays)
+    assert qsvm.qsvm_mps_point_bytes(784, 2, "fp64") == 784 * 48
+    assert qsvm.qsvm_mps_point_bytes(64, 3, "fp32") == 64 * 33 * 16
+    assert qsvm.qsvm_mps_point_bytes(64, 3, "fp32_split") == 64 * 640
+    assert qsvm.qsvm_mps_point_bytes(0, 2, "fp64") == 0 and qsvm.qsvm_mps_point_bytes(8, 4, "fp64") == 0
     assert qsvm.qsvm_mps_record_bytes(4, "fp64") == 0
     assert qsvm.qsvm_mps_record_bytes(2, 7) == 0
 
@@ -142,7 +150,7 @@ def test_configs():
                 S, st = qsvm.qsvm_config_info(c, reps, prec)
                 assert S >= 1 and 2 <= st <= 4
     S2, _ = qsvm.qsvm_config_info(1, 2, "fp32_split")
-    assert S2 == 5  # 1 KB of 192-byte records per point and chunk
+    assert S2 == 16  # 1 KB of 64-byte records per point and chunk
     assert qsvm.qsvm_get_config(2, "fp64") == -1
     qsvm.qsvm_set_config(2, "fp64", 0)
     assert qsvm.qsvm_get_config(2, "fp64") == 0

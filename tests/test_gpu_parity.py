@@ -105,7 +105,9 @@ def test_build_mps_lowprec_formats(q):
     d = _dev(X)
     f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, 3)
     f32 = q.qsvm_build_mps(d, reps, "fp32").cpu().numpy().view(np.float32).reshape(N * n, 3, 2, 4)
-    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(N * n, 2, 3, 2, 4)
+    # gauged form: two arrays (row-side a-forms, column-side b-forms) of n + 1 records of
+    # (alpha, beta) x (hi, lo) entries
+    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(2, N, n + 1, 2, 2, 4)
     # the phases T^2, P^2, P^2 T^2 with theta_{k-1} = (pi - x_{k-1})(pi - x_k) (0 at site 0)
     theta = np.concatenate([np.zeros((N, 1)), (np.pi - X[:, :-1]) * (np.pi - X[:, 1:])], axis=1).reshape(-1)
     x = X.reshape(-1)
@@ -122,11 +124,19 @@ def test_build_mps_lowprec_formats(q):
     v32 = check_forms(f32[..., 0, :], f32[..., 1, :])
     for a, b in ((v32.real, f64.real), (v32.imag, f64.imag)):
         assert np.all(np.abs(a - b) <= np.abs(b) * 2.0 ** -24 + 1e-15)
-    hi = check_forms(spl[:, 0, :, 0, :], spl[:, 0, :, 1, :])
-    lo = check_forms(spl[:, 1, :, 0, :], spl[:, 1, :, 1, :])
+    # alpha_k = conj(V2^{k-1} V0^k), beta_k = conj(V2^{k-1}) V0^k (V2^{-1} = 1) from the FP64
+    # records; the virtual site n: alpha = beta = conj(V2^{n-1})
+    V = f64.reshape(N, n, 3)
+    c = np.conj(np.concatenate([np.ones((N, 1)), V[:, :-1, 2]], axis=1))
+    want_g = np.empty((N, n + 1, 2), complex)
+    want_g[:, :n, 0] = c * np.conj(V[:, :, 0])
+    want_g[:, :n, 1] = c * V[:, :, 0]
+    want_g[:, n, 0] = want_g[:, n, 1] = np.conj(V[:, -1, 2])
+    hi = check_forms(spl[0, :, :, :, 0, :], spl[1, :, :, :, 0, :])
+    lo = check_forms(spl[0, :, :, :, 1, :], spl[1, :, :, :, 1, :])
     for part in (hi.real, hi.imag):
         assert np.array_equal(np.round(part * 2048) / 2048, part)
-    assert np.max(np.abs(hi + lo - f64)) <= 2 ** -34
+    assert np.max(np.abs(hi + lo - want_g)) <= 2 ** -34
 
 
 def test_build_mps_formats_reps3(q):
