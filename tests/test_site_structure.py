@@ -10,6 +10,11 @@ m of a bond index in bit m-1, so the last layer is the HIGH bit there).
    encode, and contracting with that pattern reproduces the state-vector kernel; at
    reps = 3 every entry is +-2^{-3/2} P^A T^B or a conjugate, in the pattern of the
    split-FP32 records at reps = 3.
+4. The gauged form of the split-FP32 records at reps = 2: after the diagonal change of
+   bond basis that makes row t = 0 of every site tensor one, both blocks of site k are
+   [[1, 1], [alpha_k, beta_k]] and the c = 1 rows are r'_s diag(1, -1) times the c = 0
+   rows with r'_0 = alpha_k, r'_1 = beta_k; contracting with those tensors plus one
+   virtual site reproduces the state-vector kernel, also where K is tiny.
 """
 import numpy as np
 import pytest
@@ -104,3 +109,57 @@ def test_reps3_phase_form(oracle):
                     pred = ((-1) ** (p1 * p2) * W[ia, ib] if s == 0
                             else (-1) ** (p1 * p2 + p2) * np.conj(W[2 - ia, 2 - ib]))
                     assert abs(val - pred) <= 1e-14, (k, s, q, p)
+
+
+def _gauged_alpha_beta(x):
+    """alpha_k = conj(V2^{k-1} V0^k), beta_k = conj(V2^{k-1}) V0^k for sites 0..n (site n
+    virtual, with V0^n = 1); V0 = T^2 and V2 = P^2 T^2 of the phase form, V2^{-1} = 1."""
+    n = len(x)
+    th = np.concatenate([_theta(x), [0.0]])
+    V0 = np.exp(-2j * th)
+    V2p = np.concatenate([[1.0], np.exp(-2j * (x + th[:n]))])
+    return np.conj(V2p) * np.conj(V0), np.conj(V2p) * V0
+
+
+def test_reps2_gauged_form(oracle):
+    """Gauge the oracle's tensors site by site: column u of site k is divided by its row-0
+    entry and row t multiplied by l_t = A_{k-1}[0][u = t] / A_{k-1}[0][u = 0] (the basis
+    change the previous site left on the bond), then compare with the gauged pattern."""
+    n = 9
+    x = inputs.mnist_like_features(1, n, 340)[0]
+    x[3] = 0.7  # a nonzero feature next to zeros, whatever the seed gives
+    A = oracle.mps_closed_form(x, 2)  # bit order: t = q + 2c, u = p + 2s
+    alpha, beta = _gauged_alpha_beta(x)
+    S = np.diag([1.0, -1.0])
+    row0 = lambda k, u: A[k, u >> 1, 0, u]  # row t = 0, column u (sigma = last-layer bit s of u)
+    for k in range(1, n - 1):
+        ell = np.array([row0(k - 1, t) / row0(k - 1, 0) for t in range(4)])
+        for s in range(2):
+            blk = {c: np.array([[ell[q + 2 * c] * A[k, s, q + 2 * c, p + 2 * s] / row0(k, p + 2 * s)
+                                 for p in range(2)] for q in range(2)]) for c in range(2)}
+            a0 = np.array([[1, 1], [alpha[k], beta[k]]])
+            assert np.max(np.abs(blk[0] - a0)) <= 1e-13, (k, s)
+            r = alpha[k] if s == 0 else beta[k]
+            assert np.max(np.abs(blk[1] - r * S @ a0)) <= 1e-13, (k, s)
+
+
+@pytest.mark.parametrize("n,seed", [(2, 341), (7, 342), (12, 343)])
+def test_reps2_gauged_contraction(oracle, n, seed):
+    """E_{k+1} blocks: G_s = E_0 + rho_s E_1 (rho_0 = alpha_i conj(alpha_j), rho_1 = beta_i
+    conj(beta_j)), E'_s = a^T G_s conj(b) with E_1 kept as S E_1 S; after the virtual site
+    n the amplitude is E_0[0][0] up to a phase, times 2^-2 per real site."""
+    X = np.concatenate([inputs.uniform_features(3, n, seed), inputs.mnist_like_features(1, n, seed)])
+    S = np.diag([1.0, -1.0])
+    for i, j in ((0, 1), (1, 2), (3, 0), (2, 2)):
+        (ai, bi), (aj, bj) = _gauged_alpha_beta(X[i]), _gauged_alpha_beta(X[j])
+        E = [np.zeros((2, 2), complex), np.zeros((2, 2), complex)]
+        E[0][0, 0] = 1.0
+        for k in range(n + 1):
+            a = np.array([[1, 1], [ai[k], bi[k]]])
+            b = np.array([[1, 1], [aj[k], bj[k]]])
+            rho = [ai[k] * np.conj(aj[k]), bi[k] * np.conj(bj[k])]
+            E = [a.T @ (E[0] + rho[s] * E[1]) @ np.conj(b) for s in range(2)]
+            E[1] = S @ E[1] @ S
+        K = abs(E[0][0, 0]) ** 2 * 2.0 ** (-4 * n)
+        Ko, _ = oracle.sv_kernel_pair(X[i], X[j], 2)
+        assert abs(K - Ko) <= 1e-13 and abs(K / Ko - 1) <= 1e-11, (n, i, j, K, Ko)
