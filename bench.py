@@ -77,9 +77,9 @@ FMA_PER_CMAC = {"fp32": 4, "fp32_split": 12, "fp64": 4}
 
 # DRAM bytes (read + write) of one pair-kernel launch, from one ncu capture of the
 # same configuration with the default pipeline shape (dram__bytes_read.sum +
-# dram__bytes_write.sum; profiles/pair_tile_split_n784_r2.md).  Configurations
-# not captured with the current kernel report null.
-MEASURED_TRAFFIC_BYTES = {}
+# dram__bytes_write.sum, one pass over the full-size launch).  Configurations not
+# captured with the current kernel report null.
+MEASURED_TRAFFIC_BYTES = {("gram_n784_r2_N8192", "fp32_split"): 13_496_331_776 + 550_258_688}
 
 
 class ClockSampler:
@@ -345,7 +345,7 @@ def run_ours(args):
     achieved = algo_flops / (kms * 1e-3) / 1e12
     mhz = SM_MAX_MHZ_NOMINAL
     if prec == "fp64":
-        peak = 1.25  # nominal GB300 FP64 (recipe table); see the design doc
+        peak = 1.25  # nominal GB300 FP64 rate (TFLOP/s)
         bound = "alu"
     else:
         peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
