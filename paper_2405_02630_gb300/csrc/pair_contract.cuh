@@ -778,16 +778,16 @@ template <>
 struct Engine<4, QSVM_FP32_SPLIT> {
   // Gauged form: both blocks of a site are [[1, 1], [alpha, beta]] (row point) and
   // conj of the column point's, block c = 1 adds the factor r'_s S (S = diag(1, -1)).
-  // Per site and s: G_s = E_0 + rho_s E_1 with rho_0 = alpha_i conj(alpha_j) and
-  // rho_1 = beta_i conj(beta_j) (E_1 is stored with the signs of S E_1 S applied);
-  // X_s[p][r] = G_s[0][r] + a[p] G_s[1][r] (a = (alpha_i, beta_i)); E'_s[p][pp] =
-  // X_s[p][0] + X_s[p][1] conj(b[pp]) (b = (alpha_j, beta_j)): 24 complex MACs and
-  // two phase products per site.  Grids: hi(rho) on 2^-kGridT, hi(E) on 2^-kGridE,
-  // hi(G) on 2^-GG, hi(X) on 2^-GX.  Exactness (|hi(alpha)|, |hi(rho)| <= 1.0004,
-  // E's components <= 1): hi(G) sums on 2^-21 with partial sums <= 3 (< 2^23 units);
-  // |G| <= 2.83, so hi(X) sums on 2^-(GG + kGridT) = 2^-21 stay below 5.67 < 8
-  // (< 2^24 units); |X| <= 5.67, so hi(E') sums on 2^-(GX + kGridT) = 2^-20 stay
-  // below 11.4 < 16.
+  // Per site: Y_c[p][r] = E_c[0][r] + a[p] E_c[1][r] (a = (alpha_i, beta_i); E_1 is
+  // stored with the signs of S E_1 S applied), shared by both s; X_s = Y_0 + rho_s Y_1
+  // with rho_0 = alpha_i conj(alpha_j), rho_1 = beta_i conj(beta_j); E'_s[p][pp] =
+  // X_s[p][0] + X_s[p][1] conj(b[pp]) (b = (alpha_j, beta_j)): 24 complex MACs and two
+  // phase products per site, and 20 re-splits (Y_1, X, E; Y_0 only seeds X).  Grids:
+  // hi(rho) on 2^-kGridT, hi(E) on 2^-kGridE, hi(Y_1) on 2^-GG, hi(X) on 2^-GX.
+  // Exactness (|hi(alpha)|, |hi(rho)| <= 1.0004, E's components <= 1): hi(Y) sums on
+  // 2^-21 with partial sums <= 3; |Y| <= 2.83, so hi(X) = hi(Y_0) + hi(rho) hi(Y_1) sums
+  // on 2^-(GG + kGridT) = 2^-21 stay below 5.67 < 8 (< 2^24 units); |X| <= 5.67, so
+  // hi(E') sums on 2^-(GX + kGridT) = 2^-20 stay below 11.4 < 16.
   static constexpr int GG = kGridG, GX = 9;
   static constexpr int kRenormEvery = 1;  // built into site()
   using Rec = Record<4, QSVM_FP32_SPLIT>;
@@ -835,35 +835,41 @@ struct Engine<4, QSVM_FP32_SPLIT> {
   }
 
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
-    float2 Rh[2], iRh[2], Rl[2], iRl[2];
-    split_rho(ra + Rec::off(0, 0), ra + Rec::off(0, 1), rb + Rec::off(0, 0), rb + Rec::off(0, 1), Rh[0], iRh[0], Rl[0],
-              iRl[0]);
-    split_rho(ra + Rec::off(1, 0), ra + Rec::off(1, 1), rb + Rec::off(1, 0), rb + Rec::off(1, 1), Rh[1], iRh[1], Rl[1],
-              iRl[1]);
-    // G_s = E_0 + rho_s E_1 in place of E_s
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const float2 e0h = Eh[0][q][r], e0l = El[0][q][r];
-        const float2 e1h = Eh[1][q][r], e1l = El[1][q][r], e1f = Ef[1][q][r];
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-          split_mix<GG>(e0h, e0l, e1h, e1l, e1f, Rh[s], iRh[s], Rl[s], iRl[s], Eh[s][q][r], El[s][q][r],
-                        Ef[s][q][r]);
-      }
-    const SplitForm A0 = form(ra, 0), A1 = form(ra, 1);
-    const SplitForm B0 = form(rb, 0), B1 = form(rb, 1);
-    float2 Nh[2][2][2], Nl[2][2][2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      float2 Xh[2][2], Xl[2][2], Xf[2][2];
+    // Y_c = a^T E_c for both blocks (Y_0 unsplit, Y_1 split onto 2^-GG)
+    float2 Y0h[2][2], Y0l[2][2], Y1h[2][2], Y1l[2][2], Y1f[2][2];
+    {
+      const SplitForm A0 = form(ra, 0), A1 = form(ra, 1);
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-          float2 hh = Eh[s][0][r], ll = El[s][0][r];
-          smac(hh, ll, Eh[s][1][r], El[s][1][r], Ef[s][1][r], p ? A1 : A0);
+          float2 hh = Eh[0][0][r], ll = El[0][0][r];
+          smac(hh, ll, Eh[0][1][r], El[0][1][r], Ef[0][1][r], p ? A1 : A0);
+          Y0h[p][r] = hh;
+          Y0l[p][r] = ll;
+          hh = Eh[1][0][r];
+          ll = El[1][0][r];
+          smac(hh, ll, Eh[1][1][r], El[1][1][r], Ef[1][1][r], p ? A1 : A0);
+          ssplit<GG>(hh, ll, Y1h[p][r], Y1l[p][r], Y1f[p][r]);
+        }
+    }
+    SplitForm R[2];
+    split_rho(ra + Rec::off(0, 0), ra + Rec::off(0, 1), rb + Rec::off(0, 0), rb + Rec::off(0, 1), R[0].h, R[0].ih,
+              R[0].l, R[0].il);
+    split_rho(ra + Rec::off(1, 0), ra + Rec::off(1, 1), rb + Rec::off(1, 0), rb + Rec::off(1, 1), R[1].h, R[1].ih,
+              R[1].l, R[1].il);
+    const SplitForm B0 = form(rb, 0), B1 = form(rb, 1);
+    float2 Nh[2][2][2], Nl[2][2][2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      // X_s = Y_0 + rho_s Y_1, then E'_s = X_s conj(b)
+      float2 Xh[2][2], Xl[2][2], Xf[2][2];
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          float2 hh = Y0h[p][r], ll = Y0l[p][r];
+          smac(hh, ll, Y1h[p][r], Y1l[p][r], Y1f[p][r], R[s]);
           ssplit<GX>(hh, ll, Xh[p][r], Xl[p][r], Xf[p][r]);
         }
 #pragma unroll
