@@ -217,6 +217,24 @@ def test_cross_leading_dimension(q, oracle):
     assert np.all(B[:, :5] == -7.0) and np.all(B[:, 26:] == -7.0)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split", "fp32"])
+@pytest.mark.parametrize("reps", [1, 2, 3])
+def test_cross_row_slice(q, prec, reps):
+    """mps + m * qsvm_mps_point_bytes as mps_a addresses points m.. of a buffer: the rows of
+    that cross kernel equal rows m.. of the full one bit for bit (the row side reads only its
+    own array, in every record format)."""
+    na, nb, n, m = 37, 21, 9, 13
+    Xa, Xb = inputs.uniform_features(na, n, 400 + reps), inputs.uniform_features(nb, n, 500 + reps)
+    A, B = q.qsvm_build_mps(_dev(Xa), reps, prec), q.qsvm_build_mps(_dev(Xb), reps, prec)
+    K, _ = q.qsvm_kernel_cross(A, na, B, nb, n, reps, prec)
+    stride = q.qsvm_mps_point_bytes(n, reps, prec)
+    assert stride % 16 == 0 and A.numel() == q.qsvm_mps_bytes(n, reps, na, prec)
+    Ks, _ = q.qsvm_kernel_cross(A[m * stride:], na - m, B, nb, n, reps, prec)
+    torch.cuda.synchronize()
+    assert q.qsvm_device_status() == 0
+    assert torch.equal(Ks, K[m:])
+
+
 # ------------------------------------------------- n = 784 (paper's size) ---
 @pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
 def test_gram_n784_mnist_like(q, oracle, prec):
