@@ -79,7 +79,7 @@ FMA_PER_CMAC = {"fp32": 4, "fp32_split": 12, "fp64": 4}
 # same configuration with the default pipeline shape (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass over the full-size launch).  Configurations not
 # captured with the current kernel report null.
-MEASURED_TRAFFIC_BYTES = {("gram_n784_r2_N8192", "fp32_split"): 13_496_331_776 + 550_258_688}
+MEASURED_TRAFFIC_BYTES = {("gram_n784_r2_N8192", "fp32_split"): 13_501_912_320 + 549_667_328}
 
 
 class ClockSampler:
