@@ -172,6 +172,28 @@ int32_t qsvm_kernel_cross(const void* mps_a, int64_t n_a, const void* mps_b, int
                           int32_t reps, int32_t precision, double* K, int64_t ldk, double* logK, int64_t ldl,
                           void* stream);
 
+/* qsvm_gram_host -- the symmetric Gram of host data, end to end: X (HOST,
+ * n_points x n_qubits float64, row-major) is copied to the device, its MPS built
+ * and its Gram computed, and K (HOST float64, ldk >= n_points) and, if logK
+ * (HOST or NULL, ldl >= n_points) is given, ln K are copied back.  Page-locked
+ * host memory lets the copies run asynchronously; pageable memory works but the
+ * copies then synchronise with the host.  The Gram runs in about eight launches of
+ * whole tile bands, alternating between `stream` and a second compute stream (they
+ * write disjoint tiles); once launches 0..c have completed, the rows of launch c
+ * are final (a band's rows receive mirror writes only from earlier bands) and a
+ * copy stream takes them to the host while later launches compute.
+ *   ws     device scratch of qsvm_gram_host_workspace_bytes(n_points, n_qubits,
+ *          reps, precision, logK != NULL) bytes, 256-byte aligned, owned by the
+ *          caller: X, the MPS and K (and logK) are staged there.
+ * Stream-ordered on `stream` (the helper streams are joined back into it): K and logK
+ * are complete once `stream` has reached this point; the call itself does not
+ * wait.  Results are bit-identical to qsvm_build_mps + qsvm_kernel_gram.
+ * Errors: as qsvm_kernel_gram, and QSVM_ERR_ARG for a missing or short ws. */
+size_t qsvm_gram_host_workspace_bytes(int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
+                                      int32_t with_logk);
+int32_t qsvm_gram_host(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
+                       double* K, int64_t ldk, double* logK, int64_t ldl, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- sharding the symmetric Gram over independent workers ----------------
  * The upper-triangle pair tiles of a Gram are independent (Sec. 5: pairs are
  * distributed evenly over GPUs and the results gathered).  A tile is a

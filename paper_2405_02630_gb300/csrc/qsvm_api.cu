@@ -336,6 +336,105 @@ int32_t qsvm_kernel_cross(const void* mps_a, int64_t n_a, const void* mps_b, int
   return QSVM_OK;
 }
 
+// ---- Gram of host data ------------------------------------------------------
+// Device scratch of qsvm_gram_host: X, the MPS, K (and logK), each 256-byte aligned.
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t qsvm_gram_host_workspace_bytes(int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
+                                      int32_t with_logk) {
+  if (n_points < 1 || n_qubits < 2) return 0;
+  const size_t mps = qsvm_mps_bytes(n_qubits, reps, n_points, precision);
+  if (mps == 0) return 0;
+  const size_t k = align256((size_t)n_points * (size_t)n_points * sizeof(double));
+  return align256((size_t)n_points * (size_t)n_qubits * sizeof(double)) + align256(mps) + k * (with_logk ? 2 : 1);
+}
+
+int32_t qsvm_gram_host(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
+                       double* K, int64_t ldk, double* logK, int64_t ldl, void* ws, size_t ws_bytes, void* stream) {
+  int32_t rc = check_common(n_qubits, reps, precision);
+  if (rc) return rc;
+  if (n_points < 1) return fail(QSVM_ERR_ARG, "n_points=%lld must be >= 1", (long long)n_points);
+  if (!X || !K) return fail(QSVM_ERR_ARG, "X and K must be non-null host pointers");
+  if (ldk < n_points) return fail(QSVM_ERR_ARG, "ldk=%lld < n_points=%lld", (long long)ldk, (long long)n_points);
+  if (logK && ldl < n_points) return fail(QSVM_ERR_ARG, "ldl=%lld < n_points=%lld", (long long)ldl, (long long)n_points);
+  const size_t need = qsvm_gram_host_workspace_bytes(n_points, n_qubits, reps, precision, logK != nullptr);
+  if (!ws || !aligned(ws, 256)) return fail(QSVM_ERR_ARG, "ws must be a non-null 256-byte aligned device pointer");
+  if (ws_bytes < need) return fail(QSVM_ERR_ARG, "ws_bytes=%zu < required %zu", ws_bytes, need);
+  const int64_t N = n_points;
+  uint8_t* base = static_cast<uint8_t*>(ws);
+  double* dX = reinterpret_cast<double*>(base);
+  base += align256((size_t)N * (size_t)n_qubits * sizeof(double));
+  void* dM = base;
+  const size_t mps_bytes = qsvm_mps_bytes(n_qubits, reps, N, precision);
+  base += align256(mps_bytes);
+  double* dK = reinterpret_cast<double*>(base);
+  double* dL = logK ? reinterpret_cast<double*>(base + align256((size_t)N * (size_t)N * sizeof(double))) : nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  cudaError_t e = cudaMemcpyAsync(dX, X, (size_t)N * (size_t)n_qubits * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy of X to the device");
+  rc = qsvm_build_mps(dX, N, n_qubits, reps, precision, dM, mps_bytes, stream);
+  if (rc) return rc;
+
+  // Chunks of whole tile bands, about kChunks of them by tile count.  Bands run in
+  // order and a band's rows receive mirror writes only from earlier bands, so the
+  // rows of chunk c are final once chunks 0..c have completed: a copy stream, which
+  // waits for each chunk in turn, copies them out while later chunks compute.  The
+  // chunks write disjoint tiles, so consecutive chunks alternate between the caller's
+  // stream and a second compute stream: a launch fills the SMs its predecessor's last
+  // wave leaves idle.
+  constexpr int kChunks = 8;
+  const int tdim = pair_tile_dim(1 << reps, precision);
+  const int64_t T = tiles_per_side(N, tdim);
+  const int64_t total = T * (T + 1) / 2;
+  const int64_t nbands = (T + kBandRows - 1) / kBandRows;
+  auto band_start = [&](int64_t b) { return b >= nbands ? total : sym_band_start(b, T); };
+  cudaStream_t cs = nullptr, xs = nullptr;  // second compute stream, copy stream
+  cudaEvent_t ev[kChunks + 3] = {};         // chunks, build, joins of cs and xs
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking);
+  for (int c = 0; e == cudaSuccess && c < kChunks + 3; ++c) e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[kChunks], st);  // the MPS is built
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[kChunks], 0);
+  int64_t b0 = 0;
+  for (int c = 0; e == cudaSuccess && rc == QSVM_OK && b0 < nbands; ++c) {
+    int64_t b1 = b0 + 1;  // the last chunk takes every remaining band
+    while (c < kChunks - 1 && b1 < nbands && band_start(b1) * kChunks < total * (int64_t)(c + 1)) ++b1;
+    if (c == kChunks - 1) b1 = nbands;
+    cudaStream_t run = (c & 1) ? cs : st;
+    rc = gram_launch(dM, N, n_qubits, reps, precision, band_start(b0), band_start(b1), dK, N, dL, N, run);
+    if (rc) break;
+    const int64_t r0 = b0 * kBandRows * tdim, r1 = std::min<int64_t>(N, b1 * kBandRows * tdim);
+    e = cudaEventRecord(ev[c], run);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, ev[c], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(K + r0 * ldk, (size_t)ldk * sizeof(double), dK + r0 * N, (size_t)N * sizeof(double),
+                            (size_t)N * sizeof(double), (size_t)(r1 - r0), cudaMemcpyDeviceToHost, xs);
+    if (e == cudaSuccess && logK)
+      e = cudaMemcpy2DAsync(logK + r0 * ldl, (size_t)ldl * sizeof(double), dL + r0 * N, (size_t)N * sizeof(double),
+                            (size_t)N * sizeof(double), (size_t)(r1 - r0), cudaMemcpyDeviceToHost, xs);
+    b0 = b1;
+  }
+  // join both helper streams back into the caller's stream (also after an error, so
+  // that nothing of this call is left unordered), then release them (deferred)
+  cudaError_t e2 = cudaSuccess;
+  cudaStream_t helpers[2] = {cs, xs};
+  for (int h = 0; h < 2; ++h) {
+    if (!helpers[h] || !ev[kChunks + 1 + h]) continue;
+    cudaError_t r = cudaEventRecord(ev[kChunks + 1 + h], helpers[h]);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(st, ev[kChunks + 1 + h], 0);
+    if (r != cudaSuccess && e2 == cudaSuccess) e2 = r;
+  }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  if (cs) cudaStreamDestroy(cs);
+  if (xs) cudaStreamDestroy(xs);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "chunked Gram or copy of K to the host");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "joining the helper streams");
+  return QSVM_OK;
+}
+
 size_t qsvm_batch_workspace_bytes(int32_t n_jobs) { return n_jobs < 1 ? 0 : ws_total(n_jobs); }
 
 int32_t qsvm_kernel_batch(const qsvm_job* jobs, int32_t n_jobs, int32_t reps, int32_t precision, void* ws,

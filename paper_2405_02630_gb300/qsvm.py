@@ -60,6 +60,8 @@ _SIGS = {
     "qsvm_build_mps": (_i32, [_dp, _i64, _i32, _i32, _i32, _vp, _sz, _vp]),
     "qsvm_kernel_gram": (_i32, [_vp, _i64, _i32, _i32, _i32, _dp, _i64, _dp, _i64, _vp]),
     "qsvm_kernel_cross": (_i32, [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _dp, _i64, _dp, _i64, _vp]),
+    "qsvm_gram_host_workspace_bytes": (_sz, [_i64, _i32, _i32, _i32, _i32]),
+    "qsvm_gram_host": (_i32, [_dp, _i64, _i32, _i32, _i32, _dp, _i64, _dp, _i64, _vp, _sz, _vp]),
     "qsvm_gram_tile_dim": (_i32, [_i32, _i32]),
     "qsvm_gram_num_tiles": (_i64, [_i64, _i32, _i32]),
     "qsvm_gram_partition": (_i32, [_i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
@@ -382,6 +384,30 @@ def qsvm_version() -> str:
 
 
 # ------------------------------------------------------------ convenience ---
+def qsvm_gram_host_workspace_bytes(n_points: int, n_qubits: int, reps: int, precision, with_logk: bool = False) -> int:
+    return int(lib().qsvm_gram_host_workspace_bytes(n_points, n_qubits, reps, _prec(precision), int(bool(with_logk))))
+
+
+def gram_host(X, reps: int, precision, K=None, logK=False, ws=None, stream=None):
+    """The Gram of host data through qsvm_gram_host.  X: contiguous CPU float64 tensor
+    (page-locked for asynchronous copies); K, logK: CPU float64 outputs (page-locked ones
+    are allocated if not given); ws: device scratch (allocated if not given).  Returns
+    (K, logK or None), complete once `stream` (default: the current stream) is synchronised."""
+    import torch
+    if X.device.type != "cpu" or X.dtype != torch.float64 or not X.is_contiguous():
+        raise ValueError("X must be a contiguous CPU float64 tensor")
+    N, n = X.shape
+    if K is None:
+        K = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+    L = torch.empty((N, N), dtype=torch.float64, pin_memory=True) if logK is True else (logK or None)
+    need = qsvm_gram_host_workspace_bytes(N, n, reps, precision, L is not None)
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    _check(lib().qsvm_gram_host(_ptr(X), N, n, reps, _prec(precision), _ptr(K), K.stride(0), _ptr(L),
+                                L.stride(0) if L is not None else 0, _ptr(ws), ws.numel(), _stream(stream)))
+    return K, L
+
+
 def gram(X, reps: int, precision, logK: bool = False, stream=None):
     """Build the MPS of every row of X and return its Gram (K, logK or None)."""
     N, n = X.shape

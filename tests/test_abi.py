@@ -198,3 +198,32 @@ def test_weak_scaling_workload_sizes():
         assert shares[0][0] == 0 and shares[-1][1] == total
         per_rank_pairs = Ng * (Ng + 1) / 2 / G
         assert abs(per_rank_pairs / (N * (N + 1) / 2) - 1) < 1e-3
+
+
+def test_gram_host_arguments():
+    """qsvm_gram_host checks its arguments on the host before any copy or launch."""
+    import ctypes
+    L = qsvm.lib()
+    v = lambda n: ctypes.c_void_p(256 * n)
+    N, n = 100, 24
+    need = qsvm.qsvm_gram_host_workspace_bytes(N, n, 2, "fp32_split")
+    a256 = lambda b: (b + 255) // 256 * 256
+    assert need == a256(N * n * 8) + a256(qsvm.qsvm_mps_bytes(n, 2, N, "fp32_split")) + a256(N * N * 8)
+    assert qsvm.qsvm_gram_host_workspace_bytes(N, n, 2, "fp32_split", True) == need + a256(N * N * 8)
+    assert qsvm.qsvm_gram_host_workspace_bytes(0, n, 2, "fp64") == 0
+    assert qsvm.qsvm_gram_host_workspace_bytes(N, n, 4, "fp64") == 0
+    ok = dict(X=v(1), N=N, n=n, reps=2, prec=2, K=v(2), ldk=N, lg=None, ldl=0, ws=v(3), wsb=need)
+    def call(**kw):
+        a = dict(ok); a.update(kw)
+        return L.qsvm_gram_host(a["X"], a["N"], a["n"], a["reps"], a["prec"], a["K"], a["ldk"], a["lg"], a["ldl"],
+                                a["ws"], a["wsb"], None)
+    assert call(X=None) == qsvm.QSVM_ERR_ARG
+    assert call(K=None) == qsvm.QSVM_ERR_ARG
+    assert call(ldk=N - 1) == qsvm.QSVM_ERR_ARG
+    assert call(lg=v(4), ldl=N - 1) == qsvm.QSVM_ERR_ARG
+    assert call(lg=v(4), ldl=N) == qsvm.QSVM_ERR_ARG  # ws sized without logK
+    assert call(ws=None) == qsvm.QSVM_ERR_ARG
+    assert call(ws=ctypes.c_void_p(256 * 3 + 16)) == qsvm.QSVM_ERR_ARG  # misaligned
+    assert call(wsb=need - 1) == qsvm.QSVM_ERR_ARG
+    assert call(N=0) == qsvm.QSVM_ERR_ARG
+    assert call(reps=4) == qsvm.QSVM_ERR_CHI
