@@ -113,7 +113,7 @@ __device__ __forceinline__ void site_row(int t, bool has_left, cd rz0, cd zzp, c
   }
 }
 
-// Phase-form records (reps = 2; split FP32 at reps = 3, see qsvm_common.cuh).
+// Phase-form records (reps = 2, FP64 and FP32).
 // At reps = 2, multiplying out the gates of one site gives
 // A^s[2q+c][2p+s] = (1/2) (-1)^{p s} e^{-i x (z(p) + z(s))} e^{-i theta (z(q) z(p) + z(c) z(s))}
 // (z(b) = 1 - 2b; the two RZ layers, the two ZZ layers with the left neighbour's
@@ -122,24 +122,19 @@ __device__ __forceinline__ void site_row(int t, bool has_left, cd rz0, cd zzp, c
 // T^2, P^2, P^2 T^2 or a conjugate: the record keeps those three phases, read off
 // the entries the gate-by-gate build produces.  The last site keeps the same
 // tensor with its right bond open (the contraction sums it at the end).  Split
-// FP32 stores the gauged form made from the same phases (qsvm_common.cuh).
-template <int CHI, int PREC>
-__device__ __forceinline__ void store_phase(uint8_t* rec, int v, cd z) {
-  using Rec = Record<CHI, PREC>;
-  if constexpr (PREC == QSVM_FP64) {  // reps = 2
+// FP32 (reps = 2 and 3) stores the gauged form made from the same phases
+// (qsvm_common.cuh).
+template <int PREC>
+__device__ __forceinline__ void store_phase(uint8_t* rec, int v, cd z) {  // reps = 2, FP64 and FP32
+  using Rec = Record<4, PREC>;
+  if constexpr (PREC == QSVM_FP64) {
     reinterpret_cast<double2*>(rec + Rec::off(v, 0))[0] = make_double2(z.re, z.im);
-  } else if constexpr (PREC == QSVM_FP32) {  // reps = 2
+  } else {
     store_forms(rec + Rec::off(v, 0), rec + Rec::off(v, 1), __double2float_rn(z.re), __double2float_rn(z.im));
-  } else {  // split FP32, reps = 3
-    constexpr double sc = (double)(1 << kGridT);
-    const double hr = rint(z.re * sc) / sc, hi = rint(z.im * sc) / sc;
-    store_forms(rec + Rec::off(v, 0, 0), rec + Rec::off(v, 1, 0), (float)hr, (float)hi);
-    store_forms(rec + Rec::off(v, 0, 1), rec + Rec::off(v, 1, 1), __double2float_rn(z.re - hr),
-                __double2float_rn(z.im - hi));
   }
 }
 
-// Gauged-form record (split FP32, reps = 2) of site k of point i: alpha and beta,
+// Gauged-form record (split FP32, reps = 2 and 3) of site k of point i: alpha and beta,
 // hi on 2^-kGridT and the lo remainder, a-form entries into the row-side array and
 // b-form entries into the column-side array (n + 1 records per point each).
 __device__ __forceinline__ void store_gauged(uint8_t* mps, int64_t n_points, int n, int64_t i, int k, cd alpha,
@@ -208,9 +203,10 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
   cd rz0, zzp, zzm;
   site_params(X, i, n, k, rz0, zzp, zzm);
   const bool has_left = k > 0;
-  if constexpr (R == 2 && PREC == QSVM_FP32_SPLIT) {
-    // gauged form: alpha_k = conj(V2^{k-1} V0^k), beta_k = conj(V2^{k-1}) V0^k
-    // (V2^{-1} = 1); the thread of the last site also writes the virtual site n
+  if constexpr ((R == 2 || R == 3) && PREC == QSVM_FP32_SPLIT) {
+    // gauged form (the same records at reps = 2 and 3): alpha_k = conj(V2^{k-1} V0^k),
+    // beta_k = conj(V2^{k-1}) V0^k with the reps = 2 phases (V2^{-1} = 1); the thread of
+    // the last site also writes the virtual site n
     cd V0, V1, V2, P0, P1, V2p = cd{1.0, 0.0};
     phases_r2(X, i, n, k, V0, V1, V2);
     if (has_left) phases_r2(X, i, n, k - 1, P0, P1, V2p);
@@ -221,45 +217,9 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
     cd V0, V1, V2;
     phases_r2(X, i, n, k, V0, V1, V2);
     uint8_t* rec = mps + gid * Record<4, PREC>::kBytes;
-    store_phase<4, PREC>(rec, 0, V0);
-    store_phase<4, PREC>(rec, 1, V1);
-    store_phase<4, PREC>(rec, 2, V2);
-  } else if constexpr (R == 3 && PREC == QSVM_FP32_SPLIT) {
-    // Rows t = 2q (c = 0), q = 0..3, right bond open; a_00[q][p] = v_q[0][2p].  With
-    // ia = p1 + p2 and ib = (q1 ^ p1) + (q2 ^ p2), W[3 ia + ib] = (-1)^{p1 p2} a_00[q][p];
-    // the entries (q, p) below cover every (ia, ib) once.  Site 0 has only t = 0, and
-    // there T = 1, so W[3 ia + ib] does not depend on ib.
-    cd a[4][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      cd v[2][CHI];
-      if (has_left || q == 0) {
-        site_row<R, false>(2 * q, has_left, rz0, zzp, zzm, v);
-      } else {
-#pragma unroll
-        for (int u = 0; u < CHI; ++u) v[0][u] = v[1][u] = cd{0.0, 0.0};
-      }
-#pragma unroll
-      for (int p = 0; p < 4; ++p) a[q][p] = v[0][2 * p];
-    }
-    const cd neg3[3] = {cd{-a[3][3].re, -a[3][3].im}, cd{-a[1][3].re, -a[1][3].im}, cd{-a[0][3].re, -a[0][3].im}};
-    cd W[9];
-    if (has_left) {
-      W[0] = a[0][0]; W[1] = a[1][0]; W[2] = a[3][0];  // ia = 0 (p = 0)
-      W[3] = a[1][1]; W[4] = a[0][1]; W[5] = a[2][1];  // ia = 1 (p = 1)
-      W[6] = neg3[0]; W[7] = neg3[1]; W[8] = neg3[2];  // ia = 2 (p = 3, sign -1)
-    } else {
-#pragma unroll
-      for (int ib = 0; ib < 3; ++ib) {
-        W[ib] = a[0][0];
-        W[3 + ib] = a[0][1];
-        W[6 + ib] = neg3[2];
-      }
-    }
-    uint8_t* rec = mps + gid * Rec::kBytes;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) store_phase<8, PREC>(rec, k, W[k]);
-    store_phase<8, PREC>(rec, 9, cmul(zzm, zzm));  // r = exp(2 i theta)
+    store_phase<PREC>(rec, 0, V0);
+    store_phase<PREC>(rec, 1, V1);
+    store_phase<PREC>(rec, 2, V2);
   } else {
     uint8_t* recA = mps + gid * Rec::kBytes;
     uint8_t* recB = recA + (Rec::kForms == 2 ? n_points * (int64_t)n * Rec::kBytes : 0);

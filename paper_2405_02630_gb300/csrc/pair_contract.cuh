@@ -942,230 +942,251 @@ struct Engine<4, QSVM_FP32_SPLIT> {
 __device__ int32_t g_pair_status;
 
 // Split FP32 at chi = 8 with four threads per pair.  One thread cannot hold a
-// pair's split environment (2 blocks x 16 entries x hi/lo/full = 192 floats) in
-// registers, so thread (s, h) of a quad owns rows {2h, 2h+1} of block s.  Per
-// site it mixes its rows of G_s = E_0 + rho_s E_1 from the same rows of E_0 and
-// E_1, publishes them in a padded shared buffer, reads all of G_s back (every
-// row is needed: X[p][r] = sum_q a[q][p] G_s[q][r]), builds its two rows of X,
-// accumulates its two rows of E'_s = X conj(b_0s) and writes them back; warp
-// barriers separate the reads and writes of the buffer.  The site tensors come in
-// phase form (nine values W and r per site, see Record<8, QSVM_FP32_SPLIT>): the
-// row side reads the value of each of its eight entries, the column side reads
-// each of the nine values once and applies it to the entries that carry it, and
-// the signs of rows and columns are folded into the rescale.  The quad agrees on
-// the power-of-two rescale through two xor-shuffles.  The grids are those of the
-// block form at chi = 8 (the stored values keep the factor 2^{-3/2}).
+// pair's split environment (2 blocks x 16 entries, hi and lo) next to its
+// working set, so the quad shares it: each thread keeps one column of both blocks
+// in registers, and the entries change hands twice per site through a 512-byte
+// buffer per pair (warp barriers separate its writes and reads).  The quad agrees
+// on the power-of-two rescale through two xor-shuffles.  The records are the
+// gauged ones of reps = 2 (the same alpha and beta; see QuadEngine below).
 template <int PREC>
 struct QuadEngine;
 
 template <>
 struct QuadEngine<QSVM_FP32_SPLIT> {
+  // Gauged form at reps = 3: both blocks of a site are the signed Kronecker square
+  // a[q][p] = (-1)^{q1 q2} M[q1][p1] M[q2][p2] of M = [[1, 1], [alpha, beta]] (q = q1 + 2 q2,
+  // p = p1 + 2 p2) and block c = 1 adds r'_s S with S = diag(1, 1, -1, -1) (r'_0 = alpha,
+  // r'_1 = beta), so with the row signs T = diag(1, 1, 1, -1) folded into the stored
+  // environment, Ev_c = T S^c E_c S^c T, a site is
+  //   Y_c = (M_i x M_i)^T Ev_c,  X_s = Y_0 + rho_s Y_1,  E'_s = X_s conj(M_j x M_j),
+  // each Kronecker product applied as two 2 x 2 stages (Z over q1, Y over q2; W over r1,
+  // E' over r2): 40 complex MACs per thread and 160 per pair per site.  Thread t of the
+  // quad owns column r = t of both blocks for the row stages and the mix, and row p = t of
+  // both X_s for the column stages; X and E' change hands through the pair's shared buffer.
+  // Grids: E's components below 1/2 after renormalisation, hi(E) on 2^-kGridE (2^-10);
+  // hi(Z) of the multiplied rows and hi(Y_1) on 2^-10 (Z and Y partial sums on 2^-21, below
+  // 1.5 and 2.9); X fully re-split onto 2^-9 (|X| <= 5.7: partial sums on 2^-21 below 2^24
+  // units); W fully re-split onto 2^-8 (|W| <= 11.4, on 2^-20); E' below 22.7 on 2^-19.
   static constexpr int CHI = 8, H = 4;
-  static constexpr int GX = grid_x(CHI);
+  static constexpr int GZ = 10, GY = 10, GX = 9, GW = 8;
   static constexpr int kRenormEvery = 1;
   using Rec = Record<CHI, QSVM_FP32_SPLIT>;
-  float* ebuf;     // this pair's environment: 32 swizzled entries (see entry()) of hi.re, hi.im, lo.re, lo.im
-  int s, h;        // block of E' and row pair this thread owns
+  float* ebuf;     // this pair's 32-entry exchange buffer (see entry())
+  int t, pi;       // thread of the quad, parity of the pair
   unsigned mask;   // the warp's active mask (all 32 lanes run the site loop together)
+  float2 Eh[2][H], El[2][H];  // column t of both blocks of the (sign-folded) environment
   int L;
 
   __device__ __forceinline__ void init(float* pair_buf, int quarter) {
     ebuf = pair_buf;
-    s = quarter >> 1;
-    h = quarter & 1;
+    t = quarter;
+    pi = (int)((threadIdx.x >> 2) & 1);
     mask = 0xffffffffu;
-    L = 0;
-    // E_0 = e_0 e_0^T: entry (c=0, q=0, r=0) = 1, all else 0; each thread clears its own rows
-    for (int p = 0; p < 2; ++p)
-      for (int r = 0; r < H; ++r) {
-        const int q = 2 * h + p;
-        *entry(s, q, r) = make_float4((s == 0 && q == 0 && r == 0) ? 1.f : 0.f, 0.f, 0.f, 0.f);
-      }
-    __syncwarp(mask);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < H; ++q) Eh[c][q] = El[c][q] = make_float2(0.f, 0.f);
+    if (t == 0) Eh[0][0].x = 1.f;  // E_0 = e_0 e_0^T
+    L = 3;  // every site() counts -3 for the factors 2^{-3/2} of a and b; the virtual site has none
   }
 
-  // Entry (c, q, r) of the pair's environment.  A 16-byte access is served a
-  // quarter-warp (two pairs) at a time; swizzling r by (2c + q/2) puts the four
-  // threads of a quad in four different 16-byte bank groups whenever they touch
-  // the same (q & 1, r) in different blocks or row pairs, and the pair stride
-  // (36 entries, 4 mod 8) moves the quarter-warp's other pair to the other four.
-  __device__ __forceinline__ float4* entry(int c, int q, int r) const {
-    return reinterpret_cast<float4*>(ebuf + (c * 16 + q * 4 + (r ^ (2 * c + (q >> 1)))) * 4);
+  // Entry (a, row, col) of the exchange buffer, 16 bytes.  The eight threads of a
+  // quarter-warp (two pairs) write (a, row, t) and read (a, t, col) for fixed (a, row) or
+  // (a, col); flipping the row's low bit and the column's high bit with the pair's parity
+  // and the column's low bit with the row's high bit puts them in eight different 16-byte
+  // bank groups in both patterns.
+  __device__ __forceinline__ float4* entry(int a, int row, int col) const {
+    return reinterpret_cast<float4*>(ebuf) + (a * 16 + 4 * (row ^ pi) + (col ^ (row >> 1) ^ (2 * pi)));
   }
 
-  // slot k = 3 ia + ib of entry (r, pp) of b_0s (and of (q, p) of a_0s): ia = p1 + p2,
-  // ib = (q1 ^ p1) + (q2 ^ p2) with q = 2 q1 + q2, p = 2 p1 + p2
-  static __host__ __device__ constexpr int slot(int q, int p) {
-    return 3 * ((p >> 1) + (p & 1)) + (((q >> 1) ^ (p >> 1)) + ((q & 1) ^ (p & 1)));
+  static __device__ __forceinline__ SplitForm form(uint32_t rec, int v) {
+    SplitForm F;
+    const float4 qh = *reinterpret_cast<const float4*>(sptr(rec + Rec::off(v, 0)));
+    const float4 ql = *reinterpret_cast<const float4*>(sptr(rec + Rec::off(v, 1)));
+    F.h = make_float2(qh.x, qh.y);
+    F.ih = make_float2(qh.z, qh.w);
+    F.l = make_float2(ql.x, ql.y);
+    F.il = make_float2(ql.z, ql.w);
+    return F;
   }
-
-  static __device__ __forceinline__ void load_value(uint32_t rec, int v, int f, float2& vh, float2& ivh, float2& vl,
-                                                    float2& ivl) {
-    const float4 qh = *reinterpret_cast<const float4*>(sptr(rec + Rec::off(v, f, 0)));
-    const float4 ql = *reinterpret_cast<const float4*>(sptr(rec + Rec::off(v, f, 1)));
-    vh = make_float2(qh.x, qh.y);
-    ivh = make_float2(qh.z, qh.w);
-    vl = make_float2(ql.x, ql.y);
-    ivl = make_float2(ql.z, ql.w);
+  // (hh, ll) += w V for a split w (hi, lo, full) and a split form of V
+  static __device__ __forceinline__ void smac(float2& hh, float2& ll, float2 wh, float2 wl, float2 wf,
+                                              const SplitForm& V) {
+    hh = fma2(bc(wh.x), V.h, hh);
+    hh = fma2(bc(wh.y), V.ih, hh);
+    ll = fma2(bc(wl.x), V.h, ll);
+    ll = fma2(bc(wl.y), V.ih, ll);
+    ll = fma2(bc(wf.x), V.l, ll);
+    ll = fma2(bc(wf.y), V.il, ll);
+  }
+  template <int GS>
+  static __device__ __forceinline__ void ssplit(float2 hh, float2 ll, float2& xh, float2& xl, float2& xf) {
+    const float2 v = add2(hh, ll);
+    xh = grid_round2<GS>(v);
+    xl = add2(fma2(xh, make_float2(-1.f, -1.f), hh), ll);  // (hh - xh) is exact
+    xf = v;
   }
 
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     const float2 m1 = make_float2(-1.f, -1.f);
-    float2 Rh[2], iRh[2], Rl[2], iRl[2];
-    split_phase(ra + Rec::off(9, 0, 0), ra + Rec::off(9, 0, 1), rb + Rec::off(9, 1, 0), rb + Rec::off(9, 1, 1), Rh,
-                iRh, Rl, iRl);
-    const float2 rh = s ? Rh[1] : Rh[0], irh = s ? iRh[1] : iRh[0];
-    const float2 rl = s ? Rl[1] : Rl[0], irl = s ? iRl[1] : iRl[0];
-    // own rows of G_s from the same rows of E_0 and E_1
-    float4 Gq[2][H];
+    SplitForm R[2];
+    split_rho(ra + Rec::off(0, 0), ra + Rec::off(0, 1), rb + Rec::off(0, 0), rb + Rec::off(0, 1), R[0].h, R[0].ih,
+              R[0].l, R[0].il);
+    split_rho(ra + Rec::off(1, 0), ra + Rec::off(1, 1), rb + Rec::off(1, 0), rb + Rec::off(1, 1), R[1].h, R[1].ih,
+              R[1].l, R[1].il);
+    // ---- rows of column t: Y_c = (M_i x M_i)^T Ev_c, X_s = Y_0 + rho_s Y_1 ----
+    float2 Xh[2][H], Xl[2][H];
+    {
+      const SplitForm A[2] = {form(ra, 0), form(ra, 1)};
+      float2 Y0h[H], Y0l[H], Y1h[H], Y1l[H], Y1f[H];
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+      for (int c = 0; c < 2; ++c) {
+        // Z[p1 + 2 q2] = Ev[2 q2] + M[p1] Ev[1 + 2 q2]: rows with q2 = 1 re-split (they are multiplied next)
+        float2 Zh[H], Zl[H], Zf[H];
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2) {
+          const float2 wh = Eh[c][1 + 2 * q2], wl = El[c][1 + 2 * q2], wf = add2(wh, wl);
+#pragma unroll
+          for (int p1 = 0; p1 < 2; ++p1) {
+            float2 hh = Eh[c][2 * q2], ll = El[c][2 * q2];
+            smac(hh, ll, wh, wl, wf, A[p1]);
+            if (q2) {
+              ssplit<GZ>(hh, ll, Zh[p1 + 2], Zl[p1 + 2], Zf[p1 + 2]);
+            } else {
+              Zh[p1] = hh;
+              Zl[p1] = ll;
+            }
+          }
+        }
+        // Y[p1 + 2 p2] = Z[p1] + M[p2] Z[p1 + 2]: Y_1 re-split (multiplied by rho next)
+#pragma unroll
+        for (int p2 = 0; p2 < 2; ++p2)
+#pragma unroll
+          for (int p1 = 0; p1 < 2; ++p1) {
+            float2 hh = Zh[p1], ll = Zl[p1];
+            smac(hh, ll, Zh[p1 + 2], Zl[p1 + 2], Zf[p1 + 2], A[p2]);
+            if (c) {
+              ssplit<GY>(hh, ll, Y1h[p1 + 2 * p2], Y1l[p1 + 2 * p2], Y1f[p1 + 2 * p2]);
+            } else {
+              Y0h[p1 + 2 * p2] = hh;
+              Y0l[p1 + 2 * p2] = ll;
+            }
+          }
+      }
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int p = 0; p < H; ++p) {
+          float2 hh = Y0h[p], ll = Y0l[p], xf;
+          smac(hh, ll, Y1h[p], Y1l[p], Y1f[p], R[s]);
+          ssplit<GX>(hh, ll, Xh[s][p], Xl[s][p], xf);
+        }
+    }
+    // ---- X changes hands: thread t takes row p = t of both X_s ----
+    __syncwarp(mask);  // every thread has read the previous site's environment entries
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < H; ++p) *entry(s, p, t) = make_float4(Xh[s][p].x, Xh[s][p].y, Xl[s][p].x, Xl[s][p].y);
+    __syncwarp(mask);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
 #pragma unroll
       for (int r = 0; r < H; ++r) {
-        const float4 v0 = *entry(0, 2 * h + j, r), v1 = *entry(1, 2 * h + j, r);
-        const float2 e1h = make_float2(v1.x, v1.y), e1l = make_float2(v1.z, v1.w);
-        float2 gh, gl, gf;
-        split_mix(make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), e1h, e1l, add2(e1h, e1l), rh, irh, rl, irl, gh,
-                  gl, gf);
-        Gq[j][r] = make_float4(gh.x, gh.y, gl.x, gl.y);
+        const float4 v = *entry(s, t, r);
+        Xh[s][r] = make_float2(v.x, v.y);
+        Xl[s][r] = make_float2(v.z, v.w);
       }
-    __syncwarp(mask);  // every thread has read its rows of the old environment
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int r = 0; r < H; ++r) *entry(s, 2 * h + j, r) = Gq[j][r];
-    __syncwarp(mask);  // G_0 and G_1 are complete
-    // X[p][r] = sum_q a[q][p] G_s[q][r] for the thread's two rows p = 2h + j, with the
-    // row signs of a_0s left out (applied in the rescale).  Block 0 uses W[k] (a-form),
-    // block 1 conj(W[8 - k]) (b-form).
-    float2 Xh[2][H], Xl[2][H], Xf[2][H];
-    {
-      float2 hh[2][H], ll[2][H];
-#pragma unroll
-      for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int r = 0; r < H; ++r) hh[p][r] = ll[p][r] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int q = 0; q < H; ++q) {
-        float2 Ah[2], iAh[2], Al[2], iAl[2];
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          const int k = slot(q, 2 * h + p);
-          load_value(ra, s ? 8 - k : k, s, Ah[p], iAh[p], Al[p], iAl[p]);
-        }
-#pragma unroll
-        for (int r = 0; r < H; ++r) {
-          const float4 gv = *entry(s, q, r);
-          const float2 g = make_float2(gv.x, gv.y), gl = make_float2(gv.z, gv.w);
-          const float2 gf = add2(g, gl);
-#pragma unroll
-          for (int p = 0; p < 2; ++p) {
-            hh[p][r] = fma2(bc(g.x), Ah[p], hh[p][r]);
-            hh[p][r] = fma2(bc(g.y), iAh[p], hh[p][r]);
-            ll[p][r] = fma2(bc(gl.x), Ah[p], ll[p][r]);
-            ll[p][r] = fma2(bc(gl.y), iAh[p], ll[p][r]);
-            ll[p][r] = fma2(bc(gf.x), Al[p], ll[p][r]);
-            ll[p][r] = fma2(bc(gf.y), iAl[p], ll[p][r]);
-          }
-        }
-      }
-#pragma unroll
-      for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int r = 0; r < H; ++r) {
-          const float2 v = add2(hh[p][r], ll[p][r]);
-          const float2 xh = grid_round2<GX>(v);
-          Xh[p][r] = xh;
-          Xl[p][r] = add2(fma2(xh, m1, hh[p][r]), ll[p][r]);
-          Xf[p][r] = v;
-        }
-    }
-    // E'_s[p][pp] = sum_r X[p][r] conj(b[r][pp]), column signs left out: conj(b_00) uses
-    // conj(W[k]) (b-form), conj(b_01) uses W[8 - k] (a-form).  Each of the nine values is
-    // loaded once and applied to the entries (r, pp) of its slot.
+    // ---- columns of row t: E'_s = X_s conj(M_j x M_j) ----
     float2 Nh[2][H], Nl[2][H];
+    {
+      const SplitForm B[2] = {form(rb, 0), form(rb, 1)};
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+      for (int s = 0; s < 2; ++s) {
+        // W[pp1 + 2 r2] = X[2 r2] + conj(M[pp1]) X[1 + 2 r2], all re-split
+        float2 Wh[H], Wl[H], Wf[H];
 #pragma unroll
-      for (int pp = 0; pp < H; ++pp) Nh[p][pp] = Nl[p][pp] = make_float2(0.f, 0.f);
+        for (int r2 = 0; r2 < 2; ++r2) {
+          const float2 wh = Xh[s][1 + 2 * r2], wl = Xl[s][1 + 2 * r2], wf = add2(wh, wl);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      float2 Bh, iBh, Bl, iBl;
-      load_value(rb, s ? 8 - k : k, 1 - s, Bh, iBh, Bl, iBl);
-#pragma unroll
-      for (int r = 0; r < H; ++r)
-#pragma unroll
-        for (int pp = 0; pp < H; ++pp) {
-          if (slot(r, pp) != k) continue;
-#pragma unroll
-          for (int p = 0; p < 2; ++p) {
-            Nh[p][pp] = fma2(bc(Xh[p][r].x), Bh, Nh[p][pp]);
-            Nh[p][pp] = fma2(bc(Xh[p][r].y), iBh, Nh[p][pp]);
-            Nl[p][pp] = fma2(bc(Xf[p][r].x), Bl, Nl[p][pp]);
-            Nl[p][pp] = fma2(bc(Xf[p][r].y), iBl, Nl[p][pp]);
-            Nl[p][pp] = fma2(bc(Xl[p][r].x), Bh, Nl[p][pp]);
-            Nl[p][pp] = fma2(bc(Xl[p][r].y), iBh, Nl[p][pp]);
+          for (int pp1 = 0; pp1 < 2; ++pp1) {
+            float2 hh = Xh[s][2 * r2], ll = Xl[s][2 * r2];
+            smac(hh, ll, wh, wl, wf, B[pp1]);
+            ssplit<GW>(hh, ll, Wh[pp1 + 2 * r2], Wl[pp1 + 2 * r2], Wf[pp1 + 2 * r2]);
           }
         }
+        // E'[pp1 + 2 pp2] = W[pp1] + conj(M[pp2]) W[pp1 + 2]
+#pragma unroll
+        for (int pp2 = 0; pp2 < 2; ++pp2)
+#pragma unroll
+          for (int pp1 = 0; pp1 < 2; ++pp1) {
+            float2 hh = Wh[pp1], ll = Wl[pp1];
+            smac(hh, ll, Wh[pp1 + 2], Wl[pp1 + 2], Wf[pp1 + 2], B[pp2]);
+            Nh[s][pp1 + 2 * pp2] = hh;
+            Nl[s][pp1 + 2 * pp2] = ll;
+          }
+      }
     }
-    // quad-wide rescale by 2^-e with the signs (-1)^{p1 p2 + p2 s} of row p and of
-    // column pp, then split onto the E grid
+    // ---- quad-wide renormalisation to components below 1/2, signs T S^s . S^s T ----
     float2 V[2][H];
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+    for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int pp = 0; pp < H; ++pp) V[p][pp] = add2(Nh[p][pp], Nl[p][pp]);
+      for (int pp = 0; pp < H; ++pp) V[s][pp] = add2(Nh[s][pp], Nl[s][pp]);
     float m = max_abs<2 * H>(reinterpret_cast<const float2(&)[2 * H]>(V));
     m = fmaxf(m, __shfl_xor_sync(mask, m, 1));
     m = fmaxf(m, __shfl_xor_sync(mask, m, 2));
     int e = 0;
     if (m > 0.f && isfinite(m)) {
       e = exp_of(m);
-      if (e < -120) {
+      if (e < -120) {  // collapse to near zero: scale up in two exact steps
         const float2 up = bc(pow2f(100));
 #pragma unroll
-        for (int p = 0; p < 2; ++p)
+        for (int s = 0; s < 2; ++s)
 #pragma unroll
           for (int pp = 0; pp < H; ++pp) {
-            Nh[p][pp] = mul2(Nh[p][pp], up);
-            Nl[p][pp] = mul2(Nl[p][pp], up);
-            V[p][pp] = mul2(V[p][pp], up);
+            Nh[s][pp] = mul2(Nh[s][pp], up);
+            Nl[s][pp] = mul2(Nl[s][pp], up);
+            V[s][pp] = mul2(V[s][pp], up);
           }
         L -= 100;
         e += 100;
       }
     }
-    const float sc = pow2f(-e);
-    __syncwarp(mask);  // every thread of the warp has read G
+    const float sc = pow2f(-(e + 1));
+    const int tt = (t == 3), ts = (t >> 1);  // T and S sign bits of row t
+    __syncwarp(mask);  // every thread has read its row of X
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+    for (int s = 0; s < 2; ++s)
 #pragma unroll
       for (int pp = 0; pp < H; ++pp) {
-        const int neg = ((h & p) ^ (p & s) ^ ((pp >> 1) & pp & 1) ^ (pp & 1 & s)) & 1;
+        const int neg = (tt ^ (pp == 3) ^ (s & (ts ^ (pp >> 1)))) & 1;
         const float2 scs = bc(neg ? -sc : sc);
-        const float2 f = mul2(V[p][pp], scs);
+        const float2 f = mul2(V[s][pp], scs);
         const float2 hv = grid_round2<kGridE>(f);
-        const float2 lv = fma2(Nl[p][pp], scs, fma2(hv, m1, mul2(Nh[p][pp], scs)));
-        *entry(s, 2 * h + p, pp) = make_float4(hv.x, hv.y, lv.x, lv.y);
+        const float2 lv = fma2(Nl[s][pp], scs, fma2(hv, m1, mul2(Nh[s][pp], scs)));
+        *entry(s, t, pp) = make_float4(hv.x, hv.y, lv.x, lv.y);
       }
-    __syncwarp(mask);  // the new environment is complete before anyone reads it
-    L += e;
+    __syncwarp(mask);
+    // ---- the new environment changes hands: thread t takes column t ----
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < H; ++q) {
+        const float4 v = *entry(c, q, t);
+        Eh[c][q] = make_float2(v.x, v.y);
+        El[c][q] = make_float2(v.z, v.w);
+      }
+    L += e + 1 - 3;
   }
 
   __device__ __forceinline__ void renorm() {}
 
-  // the last site keeps its right bond open: amplitude = sum of all entries of E
+  // after the virtual site the amplitude is entry (0, 0) of block 0 (up to a phase); the
+  // writer is thread 0 of the quad, which holds column 0
   __device__ __forceinline__ void amplitude(double& re, double& im) const {
-    re = 0.0;
-    im = 0.0;
-#pragma unroll 1
-    for (int c = 0; c < 2; ++c)
-      for (int q = 0; q < H; ++q)
-        for (int r = 0; r < H; ++r) {
-          const float4 v = *entry(c, q, r);
-          re = __dadd_rn(re, __dadd_rn((double)v.x, (double)v.z));
-          im = __dadd_rn(im, __dadd_rn((double)v.y, (double)v.w));
-        }
+    re = __dadd_rn((double)Eh[0][0].x, (double)El[0][0].x);
+    im = __dadd_rn((double)Eh[0][0].y, (double)El[0][0].y);
   }
 };
 
@@ -1183,7 +1204,7 @@ __host__ __device__ constexpr int tile_side(int chi, int prec) { return threads_
 __host__ __device__ constexpr int out_bytes(int ti) { return ti * (ti + 1) * 16; }
 // shared environment buffer of the four-thread layout: 32 entries x 16 B per pair,
 // padded to 36 entries (a stride of 4 mod 8 sixteen-byte bank groups)
-constexpr int kQuadPairFloats = 36 * 4;
+constexpr int kQuadPairFloats = 32 * 4;  // the four-thread engine's exchange buffer per pair
 __host__ __device__ constexpr int ebuf_bytes(int chi, int prec) {
   return threads_per_pair(chi, prec) == 4 ? (kTileThreads / 4) * kQuadPairFloats * 4 : 0;
 }

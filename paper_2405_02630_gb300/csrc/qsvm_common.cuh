@@ -90,27 +90,18 @@ struct Record<4, QSVM_FP32_SPLIT> {
   __host__ __device__ static constexpr int off(int v, int part) { return v * 32 + part * 16; }
 };
 
-// Phase form for split FP32 at reps = 3.  Every entry of a chi = 8 site is
-// +-2^{-3/2} P^A T^B with A, B in {3, 1, -1} (block 0) or the conjugate of one
-// (block 1); the record holds W[3 ia + ib] = 2^{-3/2} P^{3 - 2 ia} T^{3 - 2 ib}
-// (ia, ib in 0..2) and, as value 9, r = e^{2 i theta_{k-1}}: per value its a-form
-// then its b-form entry, the hi entries of all ten values, then the lo entries.
-// With q = 2 q1 + q2 and p = 2 p1 + p2 (layer 1 in the high bit):
-//   a_00[q][p] = (-1)^{p1 p2}        W[k],            k = 3 (p1 + p2) + (q1 ^ p1) + (q2 ^ p2),
-//   a_01[q][p] = (-1)^{p1 p2 + p2}   conj(W[8 - k]).
+// Split FP32 at reps = 3: the same gauged records as at reps = 2.  The change of
+// bond basis that makes row t = 0 of every site one gives, at reps = 3, both blocks
+// equal to the signed Kronecker square (-1)^{q1 q2} M[q1][p1] M[q2][p2] of
+// M = [[1, 1], [alpha_k, beta_k]] with the alpha_k, beta_k of reps = 2, and the c = 1
+// rows r'_s diag(1, 1, -1, -1) times the c = 0 rows (r'_0 = alpha_k, r'_1 = beta_k);
+// the virtual site n closes the chain the same way.
 template <>
-struct Record<8, QSVM_FP32_SPLIT> {
-  static constexpr int kForms = 1;
-  static constexpr int kValues = 10;
-  static constexpr int kValBytes = 32;
-  static constexpr int kPartBytes = kValues * kValBytes;
-  static constexpr int kBytes = 2 * kPartBytes;
-  __host__ __device__ static constexpr int off(int v, int f, int part) { return part * kPartBytes + v * kValBytes + f * 16; }
-};
+struct Record<8, QSVM_FP32_SPLIT> : Record<4, QSVM_FP32_SPLIT> {};
 
 __host__ __device__ constexpr size_t record_bytes(int chi, int prec) {
   return chi == 4 ? (prec == QSVM_FP64 ? 48 : prec == QSVM_FP32 ? 96 : 64)
-         : (chi == 8 && prec == QSVM_FP32_SPLIT) ? 640
+         : (chi == 8 && prec == QSVM_FP32_SPLIT) ? 64
                                                  : (2 * (size_t)(chi / 2) * (chi / 2) + 1) * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1);
 }
 static_assert(record_bytes(4, QSVM_FP64) == Record<4, QSVM_FP64>::kBytes, "record geometry");
@@ -125,11 +116,11 @@ static_assert(Record<2, QSVM_FP32_SPLIT>::kBytes % 16 == 0 && Record<2, QSVM_FP6
 // arrays of records a buffer holds (the FP32 block forms and the gauged form keep
 // a- and b-form arrays)
 __host__ __device__ constexpr int record_forms(int chi, int prec) {
-  return (prec == QSVM_FP64 || (chi == 4 && prec == QSVM_FP32) || (chi == 8 && prec == QSVM_FP32_SPLIT)) ? 1 : 2;
+  return (prec == QSVM_FP64 || (chi == 4 && prec == QSVM_FP32)) ? 1 : 2;
 }
 // records per point and array: one per site, plus the virtual site of the gauged form
 __host__ __device__ constexpr int record_sites(int n_qubits, int chi, int prec) {
-  return n_qubits + ((chi == 4 && prec == QSVM_FP32_SPLIT) ? 1 : 0);
+  return n_qubits + (((chi == 4 || chi == 8) && prec == QSVM_FP32_SPLIT) ? 1 : 0);
 }
 
 // ---- tile order --------------------------------------------------------------

@@ -26,9 +26,10 @@ def test_record_and_mps_bytes():
         assert qsvm.qsvm_mps_record_bytes(reps, "fp32") == entries * 16
     assert qsvm.qsvm_mps_record_bytes(1, "fp32_split") == 3 * 32
     assert qsvm.qsvm_mps_bytes(64, 3, 10, "fp32") == 2 * 10 * 64 * 33 * 16
-    # split FP32 at reps = 3, phase form: nine values and r, both forms, hi and lo, one array
-    assert qsvm.qsvm_mps_record_bytes(3, "fp32_split") == 10 * 2 * 16 * 2
-    assert qsvm.qsvm_mps_bytes(64, 3, 10, "fp32_split") == 10 * 64 * 640
+    # split FP32 at reps = 3: the gauged records of reps = 2 (alpha, beta; hi, lo; two arrays of
+    # n + 1 records per point)
+    assert qsvm.qsvm_mps_record_bytes(3, "fp32_split") == 64
+    assert qsvm.qsvm_mps_bytes(64, 3, 10, "fp32_split") == 2 * 10 * 65 * 64
     # reps = 2, phase form: three phases, (re, im) doubles or both forms of 16 bytes
     assert qsvm.qsvm_mps_record_bytes(2, "fp64") == 48
     assert qsvm.qsvm_mps_record_bytes(2, "fp32") == 96
@@ -42,7 +43,7 @@ def test_record_and_mps_bytes():
     # the row stride of one array: sites x record bytes (block form: two arrays)
     assert qsvm.qsvm_mps_point_bytes(784, 2, "fp64") == 784 * 48
     assert qsvm.qsvm_mps_point_bytes(64, 3, "fp32") == 64 * 33 * 16
-    assert qsvm.qsvm_mps_point_bytes(64, 3, "fp32_split") == 64 * 640
+    assert qsvm.qsvm_mps_point_bytes(64, 3, "fp32_split") == 65 * 64
     assert qsvm.qsvm_mps_point_bytes(0, 2, "fp64") == 0 and qsvm.qsvm_mps_point_bytes(8, 4, "fp64") == 0
     assert qsvm.qsvm_mps_record_bytes(4, "fp64") == 0
     assert qsvm.qsvm_mps_record_bytes(2, 7) == 0

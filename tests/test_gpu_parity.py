@@ -141,31 +141,26 @@ def test_build_mps_lowprec_formats(q):
 
 def test_build_mps_formats_reps3(q):
     """reps = 3: FP64 block records (the phase entry is exp(2 i theta_{k-1})); split FP32 in
-    phase form, W[3 ia + ib] = 2^{-3/2} P^{3 - 2 ia} T^{3 - 2 ib} and r, hi on the 2^-11 grid,
-    hi + lo within 2^-34 of the exact value, both forms."""
+    the gauged form, whose records are those of reps = 2 byte for byte (the reps = 3 gauge
+    gives the signed Kronecker square of the same block), with alpha_k =
+    exp(2 i (x_{k-1} + theta_{k-2} + theta_{k-1})) and beta_k with -theta_{k-1}."""
     N, n, reps = 3, 9, 3
     X = inputs.uniform_features(N, n, 91)
     d = _dev(X)
     f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, 33)
     theta = np.concatenate([np.zeros((N, 1)), (np.pi - X[:, :-1]) * (np.pi - X[:, 1:])], axis=1).reshape(-1)
     assert np.max(np.abs(f64[:, 32] - np.exp(2j * theta))) <= 1e-14
-    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(N * n, 2, 10, 2, 4)
-    x = X.reshape(-1)
-    P, T = np.exp(-1j * x), np.exp(-1j * theta)
-    want = np.stack([2 ** -1.5 * P ** a * T ** b for a in (3, 1, -1) for b in (3, 1, -1)] + [np.exp(2j * theta)], 1)
-
-    def check_forms(a, b):  # a-form (re, im, -im, re); b-form (re, -im, im, re)
-        re, im = a[..., 0], a[..., 1]
-        assert np.array_equal(a[..., 2], -im) and np.array_equal(a[..., 3], re)
-        assert np.array_equal(b[..., 0], re) and np.array_equal(b[..., 1], -im)
-        assert np.array_equal(b[..., 2], im) and np.array_equal(b[..., 3], re)
-        return re.astype(np.float64) + 1j * im.astype(np.float64)
-
-    hi = check_forms(spl[:, 0, :, 0, :], spl[:, 0, :, 1, :])
-    lo = check_forms(spl[:, 1, :, 0, :], spl[:, 1, :, 1, :])
-    for part in (hi.real, hi.imag):
-        assert np.array_equal(np.round(part * 2048) / 2048, part)
-    assert np.max(np.abs(hi + lo - want)) <= 2 ** -34
+    s3 = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy()
+    s2 = q.qsvm_build_mps(d, 2, "fp32_split").cpu().numpy()
+    assert s3.size == s2.size and np.array_equal(s3, s2)
+    spl = s3.view(np.float32).reshape(2, N, n + 1, 2, 2, 4)
+    th = np.concatenate([np.zeros((N, 1)), (np.pi - X[:, :-1]) * (np.pi - X[:, 1:]), np.zeros((N, 1))], axis=1)
+    xp = np.concatenate([np.zeros((N, 1)), X], axis=1)      # x_{k-1} (0 at site 0)
+    tp = np.concatenate([np.zeros((N, 1)), th[:, :-1]], axis=1)  # theta_{k-2}
+    want = np.stack([np.exp(2j * (xp + tp + th)), np.exp(2j * (xp + tp - th))], axis=2)
+    hi = spl[0, :, :, :, 0, 0] + 1j * spl[0, :, :, :, 0, 1].astype(np.float64)
+    lo = spl[0, :, :, :, 1, 0] + 1j * spl[0, :, :, :, 1, 1].astype(np.float64)
+    assert np.max(np.abs(hi.astype(np.complex128) + lo - want)) <= 2 ** -33
 
 
 # ----------------------------------------------------------- small Grams ---

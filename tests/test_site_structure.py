@@ -15,6 +15,10 @@ m of a bond index in bit m-1, so the last layer is the HIGH bit there).
    [[1, 1], [alpha_k, beta_k]] and the c = 1 rows are r'_s diag(1, -1) times the c = 0
    rows with r'_0 = alpha_k, r'_1 = beta_k; contracting with those tensors plus one
    virtual site reproduces the state-vector kernel, also where K is tiny.
+5. The same change of basis at reps = 3 gives the same two phases per site: both
+   blocks equal (-1)^{q1 q2} M[q1][p1] M[q2][p2] with M = [[1, 1], [alpha_k, beta_k]]
+   (a signed Kronecker square of the reps = 2 block) and the c = 1 rows are r'_s
+   diag(1, 1, -1, -1) times the c = 0 rows, r'_0 = alpha_k, r'_1 = beta_k.
 """
 import numpy as np
 import pytest
@@ -163,3 +167,28 @@ def test_reps2_gauged_contraction(oracle, n, seed):
         K = abs(E[0][0, 0]) ** 2 * 2.0 ** (-4 * n)
         Ko, _ = oracle.sv_kernel_pair(X[i], X[j], 2)
         assert abs(K - Ko) <= 1e-13 and abs(K / Ko - 1) <= 1e-11, (n, i, j, K, Ko)
+
+
+def test_reps3_gauged_form_is_a_kronecker_square(oracle):
+    """Row-0 gauge of the oracle's reps = 3 tensors (oracle bit order: q = q1 + 2 q2 with
+    q1 layer 1, the last layer in bit 2 of t and u): both blocks of site k are the signed
+    Kronecker square of the reps = 2 block [[1, 1], [alpha_k, beta_k]] with the same
+    alpha_k, beta_k, and the c = 1 rows carry r'_s diag(1, 1, -1, -1)."""
+    n = 9
+    x = inputs.uniform_features(1, n, 350)[0]
+    x[4] = 0.0  # a blank feature, as in MNIST-like data
+    A = oracle.mps_closed_form(x, 3)
+    alpha, beta = _gauged_alpha_beta(x)
+    row0 = lambda k, u: A[k, u >> 2, 0, u]
+    S = np.diag([1.0, 1.0, -1.0, -1.0])
+    for k in range(1, n - 1):
+        ell = np.array([row0(k - 1, t) / row0(k - 1, 0) for t in range(8)])
+        M = np.array([[1, 1], [alpha[k], beta[k]]])
+        kron = np.array([[(-1) ** ((q & 1) * (q >> 1)) * M[q & 1, p & 1] * M[q >> 1, p >> 1] for p in range(4)]
+                         for q in range(4)])
+        for s in range(2):
+            blk = {c: np.array([[ell[q + 4 * c] * A[k, s, q + 4 * c, p + 4 * s] / row0(k, p + 4 * s)
+                                 for p in range(4)] for q in range(4)]) for c in range(2)}
+            assert np.max(np.abs(blk[0] - kron)) <= 1e-13, (k, s)
+            r = alpha[k] if s == 0 else beta[k]
+            assert np.max(np.abs(blk[1] - r * S @ kron)) <= 1e-13, (k, s)
