@@ -98,14 +98,12 @@ enum qsvm_precision {
  * records per point in two arrays: the row-side a-forms, then the column-side
  * b-forms.
  *
- * Phase form, split FP32 at reps = 3: every entry of a chi = 8 site is
- * +-2^{-3/2} P^A T^B with A, B in {3, 1, -1} (block 0) or the conjugate of one
- * (block 1); the record holds W[3 ia + ib] = 2^{-3/2} P^{3 - 2 ia} T^{3 - 2 ib}
- * (ia, ib in 0..2) and, as value 9, r = conj(T^2), each as its a-form then its
- * b-form entry, the hi entries of the ten values then the lo entries, 640 bytes,
- * one array; the last site keeps its right bond open.  With q = 2 q1 + q2 and
- * p = 2 p1 + p2, a_00[q][p] = (-1)^{p1 p2} W[k] and
- * a_01[q][p] = (-1)^{p1 p2 + p2} conj(W[8 - k]), k = 3 (p1 + p2) + (q1 ^ p1) + (q2 ^ p2).
+ * Split FP32 at reps = 3: the gauged records of reps = 2 (the same alpha, beta and
+ * virtual site, 64 bytes per record, two arrays of n_qubits + 1 records per point).
+ * The same change of bond basis makes both blocks of a chi = 8 site the signed
+ * Kronecker square (-1)^{q1 q2} M[q1][p1] M[q2][p2] of M = [[1, 1], [alpha_k, beta_k]]
+ * (q = q1 + 2 q2, p = p1 + 2 p2, q1 the first layer) and the c = 1 rows
+ * r'_s diag(1, 1, -1, -1) times the c = 0 rows.
  *
  * Block form (reps = 1; reps = 3 in FP64 and FP32): the record stores the two chi/2 x chi/2 blocks
  * a_00, a_01, each row-major over (q, p), then the phase r_0, 16 bytes per value:
