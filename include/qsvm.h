@@ -78,25 +78,25 @@ enum qsvm_precision {
  * (the last layer is diagonal), and its blocks a_cs[q][p] = A_k[s][2q+c][2p+s]
  * satisfy a_1s = r_s a_0s with r_0 = conj(T^2) and r_1 = T^2.
  *
- * Phase form (reps = 2): every entry is +-1/2 times 1, T^2, P^2 or P^2 T^2 or a
- * conjugate, a_00 = (1/2) [[P^2 T^2, 1], [P^2, T^2]] and
+ * Phase form (reps = 2, QSVM_FP32): every entry is +-1/2 times 1, T^2, P^2 or
+ * P^2 T^2 or a conjugate, a_00 = (1/2) [[P^2 T^2, 1], [P^2, T^2]] and
  * a_01 = (1/2) [[1, -conj(P^2 T^2)], [conj(T^2), -conj(P^2)]] (rows q, columns p),
- * and the record holds the three phases V0 = T^2, V1 = P^2, V2 = P^2 T^2:
- *   QSVM_FP64        (re, im) doubles, 48 bytes;
- *   QSVM_FP32        per value its a-form then its b-form entry (below), 96 bytes.
- * The last site's tensor keeps its right bond open (its layer-1 spin is summed
- * by the contraction).  One array of records.
+ * and the record holds the three phases V0 = T^2, V1 = P^2, V2 = P^2 T^2, per
+ * value its a-form then its b-form entry (below), 96 bytes.  The last site's
+ * tensor keeps its right bond open (its layer-1 spin is summed by the
+ * contraction).  One array of records.
  *
- * Gauged form (reps = 2, QSVM_FP32_SPLIT): after the diagonal change of bond
+ * Gauged form (reps = 2, QSVM_FP64 and QSVM_FP32_SPLIT): after the diagonal change of bond
  * basis that makes row t = 0 of every site tensor one, both blocks of site k are
  * [[1, 1], [alpha_k, beta_k]] with alpha_k = conj(V2^{k-1} V0^k) and
  * beta_k = conj(V2^{k-1}) V0^k (V^k the phases of site k, V2^{-1} = 1), and
  * a_1s = r'_s diag(1, -1) a_0s with r'_0 = alpha_k, r'_1 = beta_k.  A virtual
  * site n with alpha_n = beta_n = conj(V2^{n-1}) undoes the basis change on the
- * last bond.  A record holds alpha then beta, each as its hi entry (re and im on
- * the 2^-11 grid) then its lo entry, 64 bytes; a buffer holds n_qubits + 1
- * records per point in two arrays: the row-side a-forms, then the column-side
- * b-forms.
+ * last bond.  QSVM_FP64: a record holds alpha then beta as (re, im) doubles, 32
+ * bytes, n_qubits + 1 records per point in one array.  QSVM_FP32_SPLIT: a record
+ * holds alpha then beta, each as its hi entry (re and im on the 2^-11 grid) then
+ * its lo entry, 64 bytes; a buffer holds n_qubits + 1 records per point in two
+ * arrays: the row-side a-forms, then the column-side b-forms.
  *
  * Split FP32 at reps = 3: the gauged records of reps = 2 (the same alpha, beta and
  * virtual site, 64 bytes per record, two arrays of n_qubits + 1 records per point).

@@ -113,7 +113,7 @@ __device__ __forceinline__ void site_row(int t, bool has_left, cd rz0, cd zzp, c
   }
 }
 
-// Phase-form records (reps = 2, FP64 and FP32).
+// Phase-form records (reps = 2, plain FP32).
 // At reps = 2, multiplying out the gates of one site gives
 // A^s[2q+c][2p+s] = (1/2) (-1)^{p s} e^{-i x (z(p) + z(s))} e^{-i theta (z(q) z(p) + z(c) z(s))}
 // (z(b) = 1 - 2b; the two RZ layers, the two ZZ layers with the left neighbour's
@@ -121,22 +121,24 @@ __device__ __forceinline__ void site_row(int t, bool has_left, cd rz0, cd zzp, c
 // P = e^{-i x_k}, T = e^{-i theta_{k-1}} every entry is +-1/2 times one of 1,
 // T^2, P^2, P^2 T^2 or a conjugate: the record keeps those three phases, read off
 // the entries the gate-by-gate build produces.  The last site keeps the same
-// tensor with its right bond open (the contraction sums it at the end).  Split
-// FP32 (reps = 2 and 3) stores the gauged form made from the same phases
-// (qsvm_common.cuh).
-template <int PREC>
-__device__ __forceinline__ void store_phase(uint8_t* rec, int v, cd z) {  // reps = 2, FP64 and FP32
-  using Rec = Record<4, PREC>;
-  if constexpr (PREC == QSVM_FP64) {
-    reinterpret_cast<double2*>(rec + Rec::off(v, 0))[0] = make_double2(z.re, z.im);
-  } else {
-    store_forms(rec + Rec::off(v, 0), rec + Rec::off(v, 1), __double2float_rn(z.re), __double2float_rn(z.im));
-  }
+// tensor with its right bond open (the contraction sums it at the end).  FP64 and
+// split FP32 store the gauged form made from the same phases (qsvm_common.cuh).
+__device__ __forceinline__ void store_phase(uint8_t* rec, int v, cd z) {  // reps = 2, plain FP32
+  using Rec = Record<4, QSVM_FP32>;
+  store_forms(rec + Rec::off(v, 0), rec + Rec::off(v, 1), __double2float_rn(z.re), __double2float_rn(z.im));
 }
 
 // Gauged-form record (split FP32, reps = 2 and 3) of site k of point i: alpha and beta,
 // hi on 2^-kGridT and the lo remainder, a-form entries into the row-side array and
 // b-form entries into the column-side array (n + 1 records per point each).
+// The same values in FP64: (re, im) doubles of alpha and beta, one array.
+__device__ __forceinline__ void store_gauged_fp64(uint8_t* mps, int n, int64_t i, int k, cd alpha, cd beta) {
+  using Rec = Record<4, QSVM_FP64>;
+  double2* rec = reinterpret_cast<double2*>(mps + (i * record_sites(n, 4, QSVM_FP64) + k) * Rec::kBytes);
+  rec[0] = make_double2(alpha.re, alpha.im);
+  rec[1] = make_double2(beta.re, beta.im);
+}
+
 __device__ __forceinline__ void store_gauged(uint8_t* mps, int64_t n_points, int n, int64_t i, int k, cd alpha,
                                              cd beta) {
   using Rec = Record<4, QSVM_FP32_SPLIT>;
@@ -203,23 +205,28 @@ __global__ void __launch_bounds__(256) build_mps_kernel(const double* __restrict
   cd rz0, zzp, zzm;
   site_params(X, i, n, k, rz0, zzp, zzm);
   const bool has_left = k > 0;
-  if constexpr ((R == 2 || R == 3) && PREC == QSVM_FP32_SPLIT) {
-    // gauged form (the same records at reps = 2 and 3): alpha_k = conj(V2^{k-1} V0^k),
+  if constexpr (R >= 2 && PREC != QSVM_FP32) {
+    // gauged form (FP64 and split FP32 at reps = 2 and 3): alpha_k = conj(V2^{k-1} V0^k),
     // beta_k = conj(V2^{k-1}) V0^k with the reps = 2 phases (V2^{-1} = 1); the thread of
     // the last site also writes the virtual site n
     cd V0, V1, V2, P0, P1, V2p = cd{1.0, 0.0};
     phases_r2(X, i, n, k, V0, V1, V2);
     if (has_left) phases_r2(X, i, n, k - 1, P0, P1, V2p);
     const cd c = conj_(V2p);
-    store_gauged(mps, n_points, n, i, k, cmul(c, conj_(V0)), cmul(c, V0));
-    if (k == n - 1) store_gauged(mps, n_points, n, i, n, conj_(V2), conj_(V2));
+    if constexpr (PREC == QSVM_FP64) {
+      store_gauged_fp64(mps, n, i, k, cmul(c, conj_(V0)), cmul(c, V0));
+      if (k == n - 1) store_gauged_fp64(mps, n, i, n, conj_(V2), conj_(V2));
+    } else {
+      store_gauged(mps, n_points, n, i, k, cmul(c, conj_(V0)), cmul(c, V0));
+      if (k == n - 1) store_gauged(mps, n_points, n, i, n, conj_(V2), conj_(V2));
+    }
   } else if constexpr (R == 2) {
     cd V0, V1, V2;
     phases_r2(X, i, n, k, V0, V1, V2);
     uint8_t* rec = mps + gid * Record<4, PREC>::kBytes;
-    store_phase<PREC>(rec, 0, V0);
-    store_phase<PREC>(rec, 1, V1);
-    store_phase<PREC>(rec, 2, V2);
+    store_phase(rec, 0, V0);
+    store_phase(rec, 1, V1);
+    store_phase(rec, 2, V2);
   } else {
     uint8_t* recA = mps + gid * Rec::kBytes;
     uint8_t* recB = recA + (Rec::kForms == 2 ? n_points * (int64_t)n * Rec::kBytes : 0);

@@ -542,6 +542,11 @@ __device__ __forceinline__ double2 zneg(double2 a) { return make_double2(-a.x, -
 
 template <>
 struct Engine<4, QSVM_FP64> {
+  // Gauged form (the records of split FP32 at reps = 2, in doubles): per site
+  // Y_c[p][r] = E_c[0][r] + a[p] E_c[1][r] (a = (alpha_i, beta_i), E_1 stored with the
+  // signs of S E_1 S), X_s = Y_0 + rho_s Y_1 (rho_0 = alpha_i conj(alpha_j), rho_1 =
+  // beta_i conj(beta_j)), E'_s[p][pp] = X_s[p][0] + conj(b[pp]) X_s[p][1]: 24 complex MACs
+  // and two phase products per site; the amplitude is E_0[0][0] after the virtual site.
   static constexpr int kRenormEvery = 8;
   using Rec = Record<4, QSVM_FP64>;
   double2 E[2][2][2];
@@ -555,47 +560,34 @@ struct Engine<4, QSVM_FP64> {
 #pragma unroll
         for (int r = 0; r < 2; ++r) E[c][q][r] = make_double2(0.0, 0.0);
     E[0][0][0].x = 1.0;
-    L = 0;
+    L = 2;  // every site() counts -2 for the factors 1/2 of a and b; the virtual site has none
   }
 
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     const double2* a = reinterpret_cast<const double2*>(sptr(ra));
     const double2* b = reinterpret_cast<const double2*>(sptr(rb));
-    const double2 V0 = a[0], V1 = a[1], V2 = a[2], W0 = b[0], W1 = b[1], W2 = b[2];
-    const double2 r0 = make_double2(fma(V0.x, W0.x, V0.y * W0.y), fma(V0.x, W0.y, -V0.y * W0.x));  // conj(V0) W0
-    // G_0 = T + Im(rho_0) i E_1 and G_1 = T - Im(rho_0) i E_1 with T = E_0 + Re(rho_0) E_1
+    const double2 A[2] = {a[0], a[1]};
+    const double2 Bc[2] = {zconj(b[0]), zconj(b[1])};
+    const double2 rho[2] = {zmul(A[0], Bc[0]), zmul(A[1], Bc[1])};
+    double2 Y[2][2][2];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int c = 0; c < 2; ++c)
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const double2 e0 = E[0][q][r], e1 = E[1][q][r];
-        const double tr = fma(r0.x, e1.x, e0.x), ti = fma(r0.x, e1.y, e0.y);
-        E[0][q][r] = make_double2(fma(-r0.y, e1.y, tr), fma(r0.y, e1.x, ti));
-        E[1][q][r] = make_double2(fma(r0.y, e1.y, tr), fma(-r0.y, e1.x, ti));
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) Y[c][p][r] = zfma(A[p], E[c][1][r], E[c][0][r]);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const double2 x0 = zfma(rho[s], Y[1][p][0], Y[0][p][0]);
+        const double2 x1 = zfma(rho[s], Y[1][p][1], Y[0][p][1]);
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp) {
+          const double2 v = zfma(Bc[pp], x1, x0);
+          E[s][p][pp] = (s == 1 && ((p + pp) & 1)) ? zneg(v) : v;
+        }
       }
-    double2 X[2][2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      X[0][r] = zfma(V1, E[0][1][r], zmul(V2, E[0][0][r]));
-      X[1][r] = zfma(V0, E[0][1][r], E[0][0][r]);
-    }
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      E[0][p][0] = zfma(X[p][1], zconj(W1), zmul(X[p][0], zconj(W2)));
-      E[0][p][1] = zfma(X[p][1], zconj(W0), X[p][0]);
-    }
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      X[0][r] = zfma(zconj(V0), E[1][1][r], E[1][0][r]);
-      X[1][r] = zfma(zconj(V1), E[1][1][r], zmul(zconj(V2), E[1][0][r]));  // X~[1][r]
-    }
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const double2 n0 = zfma(X[p][1], W0, X[p][0]);
-      const double2 n1 = zfma(X[p][1], W1, zmul(X[p][0], W2));
-      E[1][p][0] = p ? zneg(n0) : n0;
-      E[1][p][1] = p ? n1 : zneg(n1);
-    }
     L -= 2;
   }
 
@@ -624,18 +616,112 @@ struct Engine<4, QSVM_FP64> {
     L += e;
   }
 
+  // after the virtual site the amplitude is entry (0, 0) of block 0 (up to a phase)
   __device__ __forceinline__ void amplitude(double& re, double& im) const {
-    re = 0.0;
-    im = 0.0;
+    re = E[0][0][0].x;
+    im = E[0][0][0].y;
+  }
+};
+
+template <>
+struct Engine<8, QSVM_FP64> {
+  // Gauged form at reps = 3 (the records of reps = 2, in doubles): both blocks of a site
+  // are the signed Kronecker square of M = [[1, 1], [alpha, beta]] and block c = 1 adds
+  // r'_s diag(1, 1, -1, -1); with the row signs T = diag(1, 1, 1, -1) and the S signs
+  // folded into the stored environment, a site is Y_c = (M_i x M_i)^T E_c (two 2 x 2
+  // stages over the row bits), X_s = Y_0 + rho_s Y_1, E'_s = X_s conj(M_j x M_j) (two
+  // stages over the column bits): 160 complex MACs and two phase products.  Each stage
+  // works in place on columns, entries or rows of the environment, all in registers.
+  static constexpr int kRenormEvery = 8;
+  using Rec = Record<8, QSVM_FP64>;
+  double2 E[2][4][4];  // [c][q][r], q = q1 + 2 q2 (q1 the first layer)
+  int L;
+
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) E[c][q][r] = make_double2(0.0, 0.0);
+    E[0][0][0].x = 1.0;
+    L = 3;  // every site() counts -3 for the factors 2^{-3/2} of a and b; the virtual site has none
+  }
+
+  __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
+    const double2* a = reinterpret_cast<const double2*>(sptr(ra));
+    const double2* b = reinterpret_cast<const double2*>(sptr(rb));
+    const double2 A[2] = {a[0], a[1]};
+    const double2 Bc[2] = {zconj(b[0]), zconj(b[1])};
+    const double2 rho[2] = {zmul(A[0], Bc[0]), zmul(A[1], Bc[1])};
+    // rows: Z[p1 + 2 q2] = E[2 q2] + M[p1] E[1 + 2 q2], then Y[p1 + 2 p2] = Z[p1] + M[p2] Z[p1 + 2]
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const double2 z0 = zfma(A[0], E[c][1][r], E[c][0][r]), z1 = zfma(A[1], E[c][1][r], E[c][0][r]);
+        const double2 z2 = zfma(A[0], E[c][3][r], E[c][2][r]), z3 = zfma(A[1], E[c][3][r], E[c][2][r]);
+        E[c][0][r] = zfma(A[0], z2, z0);
+        E[c][1][r] = zfma(A[0], z3, z1);
+        E[c][2][r] = zfma(A[1], z2, z0);
+        E[c][3][r] = zfma(A[1], z3, z1);
+      }
+    // mix: X_s = Y_0 + rho_s Y_1
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const double2 y0 = E[0][p][r], y1 = E[1][p][r];
+        E[0][p][r] = zfma(rho[0], y1, y0);
+        E[1][p][r] = zfma(rho[1], y1, y0);
+      }
+    // columns: W[pp1 + 2 r2] = X[2 r2] + conj(M[pp1]) X[1 + 2 r2], then
+    // E'[pp1 + 2 pp2] = W[pp1] + conj(M[pp2]) W[pp1 + 2]; the signs T S^s . S^s T
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int p = 0; p < 2; ++p)
+      for (int p = 0; p < 4; ++p) {
+        const double2 w0 = zfma(Bc[0], E[s][p][1], E[s][p][0]), w1 = zfma(Bc[1], E[s][p][1], E[s][p][0]);
+        const double2 w2 = zfma(Bc[0], E[s][p][3], E[s][p][2]), w3 = zfma(Bc[1], E[s][p][3], E[s][p][2]);
+        const double2 nv[4] = {zfma(Bc[0], w2, w0), zfma(Bc[0], w3, w1), zfma(Bc[1], w2, w0), zfma(Bc[1], w3, w1)};
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          re = __dadd_rn(re, E[s][p][r].x);
-          im = __dadd_rn(im, E[s][p][r].y);
+        for (int pp = 0; pp < 4; ++pp) {
+          const int neg = ((p == 3) ^ (pp == 3) ^ (s & ((p >> 1) ^ (pp >> 1)))) & 1;
+          E[s][p][pp] = neg ? zneg(nv[pp]) : nv[pp];
         }
+      }
+    L -= 3;
+  }
+
+  __device__ __forceinline__ void renorm() {
+    double m = 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) m = fmax(m, fmax(fabs(E[c][q][r].x), fabs(E[c][q][r].y)));
+    if (!(m > 0.0) || !isfinite(m)) return;
+    int e;
+    frexp(m, &e);
+    if (e < -1000) e = -1000;
+    const double sc = ldexp(1.0, -e);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          E[c][q][r].x *= sc;
+          E[c][q][r].y *= sc;
+        }
+    L += e;
+  }
+
+  // after the virtual site the amplitude is entry (0, 0) of block 0 (up to a phase)
+  __device__ __forceinline__ void amplitude(double& re, double& im) const {
+    re = E[0][0][0].x;
+    im = E[0][0][0].y;
   }
 };
 
@@ -1211,7 +1297,7 @@ __host__ __device__ constexpr int ebuf_bytes(int chi, int prec) {
 
 template <int CHI, int PREC>
 __host__ __device__ constexpr int min_blocks_per_sm() {
-  return (threads_per_pair(CHI, PREC) == 4) ? 2 : (CHI >= 8) ? 1 : ((PREC == QSVM_FP32_SPLIT) ? 2 : 3);
+  return (threads_per_pair(CHI, PREC) == 4) ? 2 : (CHI >= 8) ? 1 : ((PREC == QSVM_FP32) ? 3 : 2);
 }
 
 // Shared-memory control block at the end of the dynamic allocation.

@@ -55,14 +55,14 @@ struct Record {
 // site's blocks are a_00 = (1/2) [[P^2 T^2, 1], [P^2, T^2]] and
 // a_01 = (1/2) [[1, -conj(P^2 T^2)], [conj(T^2), -conj(P^2)]] (rows q, columns p),
 // and r = conj(T^2).  A record holds the three unit phases V_0 = T^2, V_1 = P^2,
-// V_2 = P^2 T^2 (the factors 1/2 are carried in the log scale).  FP64: (re, im)
-// doubles.  FP32: per value its a-form then its b-form entry (each side of a
-// pair needs both), one array.  (Split FP32 uses the gauged form below.)
+// V_2 = P^2 T^2 (the factors 1/2 are carried in the log scale).  Plain FP32 keeps
+// them: per value its a-form then its b-form entry (each side of a pair needs both),
+// one array.  (FP64 and split FP32 use the gauged form below.)
 template <int PREC>
 struct Record<4, PREC> {
   static constexpr int H = 2;
   static constexpr int kForms = 1;
-  static constexpr int kValBytes = (PREC == QSVM_FP64) ? 16 : 32;  // one value, all its forms
+  static constexpr int kValBytes = 32;  // one value, both forms
   static constexpr int kBytes = 3 * kValBytes;
   // byte offset of value v (0: T^2, 1: P^2, 2: P^2 T^2), form f (0: a, 1: b)
   __host__ __device__ static constexpr int off(int v, int f) { return v * kValBytes + f * 16; }
@@ -82,6 +82,15 @@ struct Record<4, PREC> {
 // entry then its lo entry; the buffer keeps n + 1 records per point, an a-form
 // array (row side) and then a b-form array (column side), so each side of a pair
 // reads 64 bytes per site.
+// FP64 keeps the same values as (re, im) doubles, alpha then beta (32 bytes), in
+// one array of n + 1 records per point: each side conjugates in registers.
+template <>
+struct Record<4, QSVM_FP64> {
+  static constexpr int kForms = 1;
+  static constexpr int kBytes = 32;
+  __host__ __device__ static constexpr int off(int v) { return v * 16; }
+};
+
 template <>
 struct Record<4, QSVM_FP32_SPLIT> {
   static constexpr int kForms = 2;
@@ -90,7 +99,7 @@ struct Record<4, QSVM_FP32_SPLIT> {
   __host__ __device__ static constexpr int off(int v, int part) { return v * 32 + part * 16; }
 };
 
-// Split FP32 at reps = 3: the same gauged records as at reps = 2.  The change of
+// Split FP32 and FP64 at reps = 3: the same gauged records as at reps = 2.  The change of
 // bond basis that makes row t = 0 of every site one gives, at reps = 3, both blocks
 // equal to the signed Kronecker square (-1)^{q1 q2} M[q1][p1] M[q2][p2] of
 // M = [[1, 1], [alpha_k, beta_k]] with the alpha_k, beta_k of reps = 2, and the c = 1
@@ -98,10 +107,12 @@ struct Record<4, QSVM_FP32_SPLIT> {
 // the virtual site n closes the chain the same way.
 template <>
 struct Record<8, QSVM_FP32_SPLIT> : Record<4, QSVM_FP32_SPLIT> {};
+template <>
+struct Record<8, QSVM_FP64> : Record<4, QSVM_FP64> {};
 
 __host__ __device__ constexpr size_t record_bytes(int chi, int prec) {
-  return chi == 4 ? (prec == QSVM_FP64 ? 48 : prec == QSVM_FP32 ? 96 : 64)
-         : (chi == 8 && prec == QSVM_FP32_SPLIT) ? 64
+  return chi == 4 ? (prec == QSVM_FP64 ? 32 : prec == QSVM_FP32 ? 96 : 64)
+         : (chi == 8 && prec != QSVM_FP32) ? (prec == QSVM_FP64 ? 32 : 64)
                                                  : (2 * (size_t)(chi / 2) * (chi / 2) + 1) * 16 * (prec == QSVM_FP32_SPLIT ? 2 : 1);
 }
 static_assert(record_bytes(4, QSVM_FP64) == Record<4, QSVM_FP64>::kBytes, "record geometry");
@@ -118,9 +129,10 @@ static_assert(Record<2, QSVM_FP32_SPLIT>::kBytes % 16 == 0 && Record<2, QSVM_FP6
 __host__ __device__ constexpr int record_forms(int chi, int prec) {
   return (prec == QSVM_FP64 || (chi == 4 && prec == QSVM_FP32)) ? 1 : 2;
 }
-// records per point and array: one per site, plus the virtual site of the gauged form
+// records per point and array: one per site, plus the virtual site of the gauged
+// form (FP64 and split FP32 at reps = 2 and 3)
 __host__ __device__ constexpr int record_sites(int n_qubits, int chi, int prec) {
-  return n_qubits + (((chi == 4 || chi == 8) && prec == QSVM_FP32_SPLIT) ? 1 : 0);
+  return n_qubits + ((chi >= 4 && prec != QSVM_FP32) ? 1 : 0);
 }
 
 // ---- tile order --------------------------------------------------------------

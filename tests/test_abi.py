@@ -22,18 +22,22 @@ def test_record_and_mps_bytes():
     # the phase r, 16 bytes each; split FP32 holds hi and lo; FP32 formats hold two forms
     for reps, chi in ((1, 2), (3, 8)):
         entries = 2 * (chi // 2) ** 2 + 1  # blocks a_00, a_01 and the phase r
-        assert qsvm.qsvm_mps_record_bytes(reps, "fp64") == entries * 16
         assert qsvm.qsvm_mps_record_bytes(reps, "fp32") == entries * 16
+    assert qsvm.qsvm_mps_record_bytes(1, "fp64") == 3 * 16
+    # FP64 at reps = 3: the gauged records of reps = 2 (alpha, beta doubles, n + 1 per point)
+    assert qsvm.qsvm_mps_record_bytes(3, "fp64") == 32
+    assert qsvm.qsvm_mps_bytes(64, 3, 10, "fp64") == 10 * 65 * 32
     assert qsvm.qsvm_mps_record_bytes(1, "fp32_split") == 3 * 32
     assert qsvm.qsvm_mps_bytes(64, 3, 10, "fp32") == 2 * 10 * 64 * 33 * 16
     # split FP32 at reps = 3: the gauged records of reps = 2 (alpha, beta; hi, lo; two arrays of
     # n + 1 records per point)
     assert qsvm.qsvm_mps_record_bytes(3, "fp32_split") == 64
     assert qsvm.qsvm_mps_bytes(64, 3, 10, "fp32_split") == 2 * 10 * 65 * 64
-    # reps = 2, phase form: three phases, (re, im) doubles or both forms of 16 bytes
-    assert qsvm.qsvm_mps_record_bytes(2, "fp64") == 48
+    # reps = 2: plain FP32 in phase form (three phases, both forms of 16 bytes); FP64 in gauged
+    # form (alpha, beta doubles, n + 1 records per point, one array)
+    assert qsvm.qsvm_mps_record_bytes(2, "fp64") == 32
     assert qsvm.qsvm_mps_record_bytes(2, "fp32") == 96
-    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp64") == 8192 * 784 * 48
+    assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp64") == 8192 * 785 * 32
     assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32") == 8192 * 784 * 96
     # reps = 2, split FP32, gauged form: alpha and beta, hi and lo, per form; n + 1 records
     # (one virtual site) per point in a row-side and a column-side array
@@ -41,7 +45,7 @@ def test_record_and_mps_bytes():
     assert qsvm.qsvm_mps_point_bytes(784, 2, "fp32_split") == 785 * 64
     assert qsvm.qsvm_mps_bytes(784, 2, 8192, "fp32_split") == 2 * 8192 * 785 * 64
     # the row stride of one array: sites x record bytes (block form: two arrays)
-    assert qsvm.qsvm_mps_point_bytes(784, 2, "fp64") == 784 * 48
+    assert qsvm.qsvm_mps_point_bytes(784, 2, "fp64") == 785 * 32
     assert qsvm.qsvm_mps_point_bytes(64, 3, "fp32") == 64 * 33 * 16
     assert qsvm.qsvm_mps_point_bytes(64, 3, "fp32_split") == 65 * 64
     assert qsvm.qsvm_mps_point_bytes(0, 2, "fp64") == 0 and qsvm.qsvm_mps_point_bytes(8, 4, "fp64") == 0

@@ -45,7 +45,7 @@ def test_c_program_against_header(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0, out.stderr
     lines = dict(line.split(" ", 1) for line in out.stdout.strip().splitlines())
-    assert lines["record"] == "48 96 64"
+    assert lines["record"] == "32 96 64"
     assert int(lines["mps"]) == 2 * 8192 * 785 * 64
     total, begin, end, tdim = map(int, lines["tiles"].split())
     assert tdim == 16 and total == 512 * 513 // 2 and 0 < begin < end == total

@@ -33,36 +33,70 @@ def _dev(X):
 
 
 def _decode_fp64(buf, N, n, reps):
-    """Site tensors A[i, k, sigma, t, u] from FP64 records (layouts of include/qsvm.h).
-    Block form (reps 1, 3): a_0s[q][p] = A[s][2q][2p+s], then r; the rows with c = 1 are
-    a_1s = r_s a_0s with r_0 = r, r_1 = conj(r).  Phase form (reps 2): V0 = T^2, V1 = P^2,
-    V2 = P^2 T^2 give a_00 = [[V2, 1], [V1, V0]] / 2, a_01 = [[1, -conj V2], [conj V0, -conj V1]] / 2
-    and r = conj(V0); the last site's right bond is left open."""
+    """Site tensors A[i, k, sigma, t, u] and last-bond weights w[i, u] (None: the last bond is
+    summed) from FP64 records (layouts of include/qsvm.h), with t = 2q + c, u = 2p + s.
+    Block form (reps 1): a_0s[q][p] = A[s][2q][2p+s], then r; the rows with c = 1 are
+    a_1s = r_s a_0s with r_0 = r, r_1 = conj(r).  Gauged form (reps 2): records k = 0..n of
+    (alpha, beta) give a_0s = [[1, 1], [alpha, beta]] and a_1s = r'_s diag(1, -1) a_0s with
+    r'_0 = alpha, r'_1 = beta; the virtual record n gives the weights of the last bond,
+    w = (1, alpha_n, alpha_n, -alpha_n^2), and the state is 2^-n times the contraction, up to
+    a global phase."""
     chi = 2 ** reps
     H = chi // 2
     A = np.zeros((N, n, 2, chi, chi), complex)
+    w = None
+    if reps == 3:
+        # gauged, t = q + 4c and u = p + 4s with q = q1 + 2 q2: both blocks are
+        # (-1)^{q1 q2} M[q1][p1] M[q2][p2] with M = [[1, 1], [alpha, beta]]; the c = 1 rows are
+        # r'_s (-1)^{q2} times them; the virtual site weights the last bond
+        raw = buf.cpu().numpy().view(np.complex128).reshape(N, n + 1, 2)
+        al, be = raw[..., 0], raw[..., 1]
+        def kr(a, b, q, p):
+            m = lambda x, y: np.ones_like(a) if x == 0 else (a if y == 0 else b)
+            return (-1) ** ((q & 1) * (q >> 1)) * m(q & 1, p & 1) * m(q >> 1, p >> 1)
+        for s_ in range(2):
+            rs = al[:, :n] if s_ == 0 else be[:, :n]
+            for qq in range(4):
+                for p in range(4):
+                    v = kr(al[:, :n], be[:, :n], qq, p)
+                    A[:, :, s_, qq, p + 4 * s_] = v
+                    A[:, :, s_, qq + 4, p + 4 * s_] = rs * (1 - 2 * (qq >> 1)) * v
+        an = al[:, n]
+        w = np.zeros((N, 8), complex)
+        for p in range(4):
+            v0 = kr(an, an, p, 0)
+            w[:, p] = v0
+            w[:, p + 4] = an * (1 - 2 * (p >> 1)) * v0
+        return A, w * 2.0 ** (-1.5 * n)
     if reps == 2:
-        raw = buf.cpu().numpy().view(np.complex128).reshape(N, n, 3)
-        V0, V1, V2 = raw[..., 0], raw[..., 1], raw[..., 2]
-        one = np.ones_like(V0)
-        blocks = [np.stack([np.stack([V2, one], -1), np.stack([V1, V0], -1)], -2) / 2,
-                  np.stack([np.stack([one, -np.conj(V2)], -1), np.stack([np.conj(V0), -np.conj(V1)], -1)], -2) / 2]
-        r = np.conj(V0)
-    else:
-        raw = buf.cpu().numpy().view(np.complex128).reshape(N, n, 2 * H * H + 1)
-        blocks = [raw[:, :, s * H * H:(s + 1) * H * H].reshape(N, n, H, H) for s in range(2)]
-        r = raw[:, :, 2 * H * H]
+        raw = buf.cpu().numpy().view(np.complex128).reshape(N, n + 1, 2)
+        al, be = raw[..., 0], raw[..., 1]
+        one = np.ones_like(al[:, :n])
+        blocks = [np.stack([np.stack([one, one], -1), np.stack([al[:, :n], be[:, :n]], -1)], -2)] * 2
+        for s_ in range(2):
+            rs = al[:, :n] if s_ == 0 else be[:, :n]
+            for qq in range(H):
+                for p in range(H):
+                    A[:, :, s_, 2 * qq, 2 * p + s_] = blocks[s_][:, :, qq, p]
+                    A[:, :, s_, 2 * qq + 1, 2 * p + s_] = rs * (1 - 2 * qq) * blocks[s_][:, :, qq, p]
+        an = al[:, n]
+        w = np.stack([np.ones_like(an), an, an, -an * an], -1) * 2.0 ** (-n)
+        return A, w
+    raw = buf.cpu().numpy().view(np.complex128).reshape(N, n, 2 * H * H + 1)
+    blocks = [raw[:, :, s * H * H:(s + 1) * H * H].reshape(N, n, H, H) for s in range(2)]
+    r = raw[:, :, 2 * H * H]
     for s in range(2):
         rs = r if s == 0 else np.conj(r)
         for qq in range(H):
             for p in range(H):
                 A[:, :, s, 2 * qq, 2 * p + s] = blocks[s][:, :, qq, p]
                 A[:, :, s, 2 * qq + 1, 2 * p + s] = rs * blocks[s][:, :, qq, p]
-    return A
+    return A, w
 
 
-def _mps_state(A):
-    """Contract one point's site tensors A[k, sigma, t, u] to the 2^n state (qubit k = bit k)."""
+def _mps_state(A, w=None):
+    """Contract one point's site tensors A[k, sigma, t, u] to the 2^n state (qubit k = bit k);
+    the last bond is summed, or weighted by w."""
     n, _, chi, _ = A.shape
     psi = np.zeros(2 ** n, complex)
     for s in range(2 ** n):
@@ -70,7 +104,7 @@ def _mps_state(A):
         v[0] = 1.0
         for k in range(n):
             v = v @ A[k, (s >> k) & 1]
-        psi[s] = v.sum()  # last site: right bond carries sigma; A vanishes off u == sigma
+        psi[s] = v.sum() if w is None else v @ w
     return psi
 
 
@@ -92,10 +126,14 @@ def test_build_mps_reproduces_state_vector(q, oracle, n, reps):
     X = inputs.uniform_features(3, n, 1000 + 10 * n + reps)
     buf = q.qsvm_build_mps(_dev(X), reps, "fp64")
     torch.cuda.synchronize()
-    A = _decode_fp64(buf, 3, n, reps)
+    A, w = _decode_fp64(buf, 3, n, reps)
     for i in range(3):
-        psi = _mps_state(A[i])
+        psi = _mps_state(A[i], None if w is None else w[i])
         ref = oracle.sv_state(X[i], reps)
+        if w is not None:  # the gauged form fixes the state up to a global phase
+            ph = np.vdot(psi, ref)
+            assert abs(abs(ph) - 1.0) <= 1e-12
+            psi = psi * ph / abs(ph)
         assert np.max(np.abs(psi - ref)) <= 1e-12
 
 
@@ -103,16 +141,21 @@ def test_build_mps_lowprec_formats(q):
     N, n, reps = 5, 33, 2
     X = inputs.mnist_like_features(N, n, 77)
     d = _dev(X)
-    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, 3)
+    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N, n + 1, 2)
     f32 = q.qsvm_build_mps(d, reps, "fp32").cpu().numpy().view(np.float32).reshape(N * n, 3, 2, 4)
-    # gauged form: two arrays (row-side a-forms, column-side b-forms) of n + 1 records of
-    # (alpha, beta) x (hi, lo) entries
-    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(2, N, n + 1, 2, 2, 4)
     # the phases T^2, P^2, P^2 T^2 with theta_{k-1} = (pi - x_{k-1})(pi - x_k) (0 at site 0)
     theta = np.concatenate([np.zeros((N, 1)), (np.pi - X[:, :-1]) * (np.pi - X[:, 1:])], axis=1).reshape(-1)
     x = X.reshape(-1)
     want = np.stack([np.exp(-2j * theta), np.exp(-2j * x), np.exp(-2j * (x + theta))], axis=1)
-    assert np.max(np.abs(f64 - want)) <= 1e-14
+    # gauged values: alpha_k = conj(V2^{k-1} V0^k), beta_k = conj(V2^{k-1}) V0^k (V2^{-1} = 1);
+    # the virtual site n: alpha = beta = conj(V2^{n-1})
+    V = want.reshape(N, n, 3)
+    c = np.conj(np.concatenate([np.ones((N, 1)), V[:, :-1, 2]], axis=1))
+    want_g = np.empty((N, n + 1, 2), complex)
+    want_g[:, :n, 0] = c * np.conj(V[:, :, 0])
+    want_g[:, :n, 1] = c * V[:, :, 0]
+    want_g[:, n, 0] = want_g[:, n, 1] = np.conj(V[:, -1, 2])
+    assert np.max(np.abs(f64 - want_g)) <= 1e-14
 
     def check_forms(a, b):  # a-form (re, im, -im, re); b-form (re, -im, im, re)
         re, im = a[..., 0], a[..., 1]
@@ -122,34 +165,29 @@ def test_build_mps_lowprec_formats(q):
         return re.astype(np.float64) + 1j * im.astype(np.float64)
 
     v32 = check_forms(f32[..., 0, :], f32[..., 1, :])
-    for a, b in ((v32.real, f64.real), (v32.imag, f64.imag)):
+    for a, b in ((v32.real, want.real), (v32.imag, want.imag)):
         assert np.all(np.abs(a - b) <= np.abs(b) * 2.0 ** -24 + 1e-15)
-    # alpha_k = conj(V2^{k-1} V0^k), beta_k = conj(V2^{k-1}) V0^k (V2^{-1} = 1) from the FP64
-    # records; the virtual site n: alpha = beta = conj(V2^{n-1})
-    V = f64.reshape(N, n, 3)
-    c = np.conj(np.concatenate([np.ones((N, 1)), V[:, :-1, 2]], axis=1))
-    want_g = np.empty((N, n + 1, 2), complex)
-    want_g[:, :n, 0] = c * np.conj(V[:, :, 0])
-    want_g[:, :n, 1] = c * V[:, :, 0]
-    want_g[:, n, 0] = want_g[:, n, 1] = np.conj(V[:, -1, 2])
+    # split: two arrays (row-side a-forms, column-side b-forms) of n + 1 records of
+    # (alpha, beta) x (hi, lo) entries, the same values as the FP64 records
+    spl = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy().view(np.float32).reshape(2, N, n + 1, 2, 2, 4)
     hi = check_forms(spl[0, :, :, :, 0, :], spl[1, :, :, :, 0, :])
     lo = check_forms(spl[0, :, :, :, 1, :], spl[1, :, :, :, 1, :])
     for part in (hi.real, hi.imag):
         assert np.array_equal(np.round(part * 2048) / 2048, part)
-    assert np.max(np.abs(hi + lo - want_g)) <= 2 ** -34
+    assert np.max(np.abs(hi + lo - f64)) <= 2 ** -34
 
 
 def test_build_mps_formats_reps3(q):
-    """reps = 3: FP64 block records (the phase entry is exp(2 i theta_{k-1})); split FP32 in
-    the gauged form, whose records are those of reps = 2 byte for byte (the reps = 3 gauge
+    """reps = 3: FP64 and split FP32 in the gauged form, whose records are those of reps = 2
+    byte for byte (the reps = 3 gauge
     gives the signed Kronecker square of the same block), with alpha_k =
     exp(2 i (x_{k-1} + theta_{k-2} + theta_{k-1})) and beta_k with -theta_{k-1}."""
     N, n, reps = 3, 9, 3
     X = inputs.uniform_features(N, n, 91)
     d = _dev(X)
-    f64 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy().view(np.complex128).reshape(N * n, 33)
-    theta = np.concatenate([np.zeros((N, 1)), (np.pi - X[:, :-1]) * (np.pi - X[:, 1:])], axis=1).reshape(-1)
-    assert np.max(np.abs(f64[:, 32] - np.exp(2j * theta))) <= 1e-14
+    f3 = q.qsvm_build_mps(d, reps, "fp64").cpu().numpy()
+    f2 = q.qsvm_build_mps(d, 2, "fp64").cpu().numpy()
+    assert f3.size == f2.size and np.array_equal(f3, f2)  # FP64: the gauged records of reps = 2
     s3 = q.qsvm_build_mps(d, reps, "fp32_split").cpu().numpy()
     s2 = q.qsvm_build_mps(d, 2, "fp32_split").cpu().numpy()
     assert s3.size == s2.size and np.array_equal(s3, s2)
