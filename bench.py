@@ -58,12 +58,12 @@ def factorized_cmacs_per_entry(n: int, reps: int, prec: str = "fp64") -> int:
     """Complex MACs per kernel entry of the contraction as the kernels carry it out.
     Block form (reps 1, 3): per site rho = r(i) conj(r(j)) (1), G_s = E_0 + rho_s E_1
     (chi^2/2), X_s = a_0s^T G_s and E'_s = X_s conj(b_0s) (chi^3/4 each), bonds padded to chi.
-    Phase form (reps 2, FP64 and FP32): rho (1), G (8), X and E' with the unit entries of a
-    and b added rather than multiplied (12 each): 33.  Gauged form (split FP32), n + 1 sites
+    Phase form (reps 2, plain FP32): rho (1), G (8), X and E' with the unit entries of a and b
+    added rather than multiplied (12 each): 33.  Gauged form (FP64 and split FP32), n + 1 sites
     (one virtual): reps 2, two phase products, Y (8), X (8), E' (8): 26 per site; reps 3, the
     Kronecker stages Z, Y (32 each), the mix (32), W, E' (32 each) and two phase products: 162."""
     chi = 2 ** reps
-    if prec == "fp32_split" and reps in (2, 3):
+    if prec in ("fp32_split", "fp64") and reps in (2, 3):
         return (n + 1) * (26 if reps == 2 else 162)
     if reps == 2:
         return n * 33
