@@ -868,13 +868,14 @@ struct Engine<4, QSVM_FP32_SPLIT> {
   // stored with the signs of S E_1 S applied), shared by both s; X_s = Y_0 + rho_s Y_1
   // with rho_0 = alpha_i conj(alpha_j), rho_1 = beta_i conj(beta_j); E'_s[p][pp] =
   // X_s[p][0] + X_s[p][1] conj(b[pp]) (b = (alpha_j, beta_j)): 24 complex MACs and two
-  // phase products per site, and 20 re-splits (Y_1, X, E; Y_0 only seeds X).  Grids:
-  // hi(rho) on 2^-kGridT, hi(E) on 2^-kGridE, hi(Y_1) on 2^-GG, hi(X) on 2^-GX.
-  // Exactness (|hi(alpha)|, |hi(rho)| <= 1.0004, E's components <= 1): hi(Y) sums on
-  // 2^-21 with partial sums <= 3; |Y| <= 2.83, so hi(X) = hi(Y_0) + hi(rho) hi(Y_1) sums
-  // on 2^-(GG + kGridT) = 2^-21 stay below 5.67 < 8 (< 2^24 units); |X| <= 5.67, so
-  // hi(E') sums on 2^-(GX + kGridT) = 2^-20 stay below 11.4 < 16.
-  static constexpr int GG = kGridG, GX = 9;
+  // phase products per site, and 16 re-splits (Y_1, X[.][1], E; Y_0 and X[.][0] only
+  // seed the next sum).  Grids: hi(rho) on 2^-kGridT, hi(E) on 2^-kGridE, hi(Y_1) on
+  // 2^-GG, hi(X[.][1]) on 2^-GX.  Exactness (|hi(alpha)|, |hi(rho)| <= 1.0004, E's
+  // components below 1/2 after renormalisation): hi(Y) sums on 2^-21 with partial sums
+  // <= 1.5; |Y| <= 1.42, so hi(X) = hi(Y_0) + hi(rho) hi(Y_1) sums on 2^-21 stay below
+  // 2.84; |X| <= 2.84, so hi(E') = hi(X[.][0]) + hi(X[.][1]) hi(conj b) sums on
+  // 2^-(GX + kGridT) = 2^-21 stay below 5.7 < 8 (< 2^24 units).
+  static constexpr int GG = kGridG, GX = 10;
   static constexpr int kRenormEvery = 1;  // built into site()
   using Rec = Record<4, QSVM_FP32_SPLIT>;
   float2 Eh[2][2][2], El[2][2][2], Ef[2][2][2];  // Ef = fl(Eh + El)
@@ -956,7 +957,12 @@ struct Engine<4, QSVM_FP32_SPLIT> {
         for (int r = 0; r < 2; ++r) {
           float2 hh = Y0h[p][r], ll = Y0l[p][r];
           smac(hh, ll, Y1h[p][r], Y1l[p][r], Y1f[p][r], R[s]);
-          ssplit<GX>(hh, ll, Xh[p][r], Xl[p][r], Xf[p][r]);
+          if (r) {
+            ssplit<GX>(hh, ll, Xh[p][r], Xl[p][r], Xf[p][r]);
+          } else {  // seeds E'_s[p][.]
+            Xh[p][r] = hh;
+            Xl[p][r] = ll;
+          }
         }
 #pragma unroll
       for (int p = 0; p < 2; ++p)
@@ -968,7 +974,8 @@ struct Engine<4, QSVM_FP32_SPLIT> {
           Nl[s][p][pp] = ll;
         }
     }
-    // renormalise by 2^-e, apply the signs (-1)^{p+pp} of S E_1 S, re-split onto the E grid
+    // renormalise by 2^-(e+1) (components below 1/2), apply the signs (-1)^{p+pp} of
+    // S E_1 S, re-split onto the E grid
     const float2 m1 = make_float2(-1.f, -1.f);
     float2 V[2][2][2];
 #pragma unroll
@@ -997,7 +1004,7 @@ struct Engine<4, QSVM_FP32_SPLIT> {
         e += 100;
       }
     }
-    const float sc = pow2f(-e);
+    const float sc = pow2f(-(e + 1));
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -1011,7 +1018,7 @@ struct Engine<4, QSVM_FP32_SPLIT> {
           El[s][p][r] = fma2(Nl[s][p][r], scs, fma2(h, m1, mul2(Nh[s][p][r], scs)));
           Ef[s][p][r] = f;
         }
-    L += e - 2;
+    L += e + 1 - 2;
   }
 
   __device__ __forceinline__ void renorm() {}
