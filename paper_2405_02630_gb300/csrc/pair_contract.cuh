@@ -1056,12 +1056,14 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
   // E' over r2): 40 complex MACs per thread and 160 per pair per site.  Thread t of the
   // quad owns column r = t of both blocks for the row stages and the mix, and row p = t of
   // both X_s for the column stages; X and E' change hands through the pair's shared buffer.
-  // Grids: E's components below 1/2 after renormalisation, hi(E) on 2^-kGridE (2^-10);
-  // hi(Z) of the multiplied rows and hi(Y_1) on 2^-10 (Z and Y partial sums on 2^-21, below
-  // 1.5 and 2.9); X fully re-split onto 2^-9 (|X| <= 5.7: partial sums on 2^-21 below 2^24
-  // units); W fully re-split onto 2^-8 (|W| <= 11.4, on 2^-20); E' below 22.7 on 2^-19.
+  // Grids: E's components below 1/4 after renormalisation, hi(E) on 2^-GE (2^-11);
+  // hi(Z) of the multiplied rows and hi(Y_1) on 2^-10 (Z and Y partial sums on 2^-22,
+  // below 0.75 and 1.5; X = Y_0 + rho Y_1 on 2^-22, below 2.9); X fully re-split onto 2^-9
+  // (it changes hands); W's multiplied entries re-split onto 2^-9, its other entries seed
+  // E' unsplit (|W| <= 5.7 on 2^-20); E' below 11.4 on 2^-20: every partial sum stays
+  // below 2^24 units.
   static constexpr int CHI = 8, H = 4;
-  static constexpr int GZ = 10, GY = 10, GX = 9, GW = 8;
+  static constexpr int GE = 11, GZ = 10, GY = 10, GX = 9, GW = 9;
   static constexpr int kRenormEvery = 1;
   using Rec = Record<CHI, QSVM_FP32_SPLIT>;
   float* ebuf;     // this pair's 32-entry exchange buffer (see entry())
@@ -1196,7 +1198,8 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
       const SplitForm B[2] = {form(rb, 0), form(rb, 1)};
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        // W[pp1 + 2 r2] = X[2 r2] + conj(M[pp1]) X[1 + 2 r2], all re-split
+        // W[pp1 + 2 r2] = X[2 r2] + conj(M[pp1]) X[1 + 2 r2]: entries with r2 = 1 re-split
+        // (they are multiplied next), the others seed E'
         float2 Wh[H], Wl[H], Wf[H];
 #pragma unroll
         for (int r2 = 0; r2 < 2; ++r2) {
@@ -1205,7 +1208,12 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
           for (int pp1 = 0; pp1 < 2; ++pp1) {
             float2 hh = Xh[s][2 * r2], ll = Xl[s][2 * r2];
             smac(hh, ll, wh, wl, wf, B[pp1]);
-            ssplit<GW>(hh, ll, Wh[pp1 + 2 * r2], Wl[pp1 + 2 * r2], Wf[pp1 + 2 * r2]);
+            if (r2) {
+              ssplit<GW>(hh, ll, Wh[pp1 + 2], Wl[pp1 + 2], Wf[pp1 + 2]);
+            } else {
+              Wh[pp1] = hh;
+              Wl[pp1] = ll;
+            }
           }
         }
         // E'[pp1 + 2 pp2] = W[pp1] + conj(M[pp2]) W[pp1 + 2]
@@ -1220,7 +1228,7 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
           }
       }
     }
-    // ---- quad-wide renormalisation to components below 1/2, signs T S^s . S^s T ----
+    // ---- quad-wide renormalisation to components below 1/4, signs T S^s . S^s T ----
     float2 V[2][H];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -1246,7 +1254,7 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
         e += 100;
       }
     }
-    const float sc = pow2f(-(e + 1));
+    const float sc = pow2f(-(e + 2));
     const int tt = (t == 3), ts = (t >> 1);  // T and S sign bits of row t
     __syncwarp(mask);  // every thread has read its row of X
 #pragma unroll
@@ -1256,7 +1264,7 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
         const int neg = (tt ^ (pp == 3) ^ (s & (ts ^ (pp >> 1)))) & 1;
         const float2 scs = bc(neg ? -sc : sc);
         const float2 f = mul2(V[s][pp], scs);
-        const float2 hv = grid_round2<kGridE>(f);
+        const float2 hv = grid_round2<GE>(f);
         const float2 lv = fma2(Nl[s][pp], scs, fma2(hv, m1, mul2(Nh[s][pp], scs)));
         *entry(s, t, pp) = make_float4(hv.x, hv.y, lv.x, lv.y);
       }
@@ -1270,7 +1278,7 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
         Eh[c][q] = make_float2(v.x, v.y);
         El[c][q] = make_float2(v.z, v.w);
       }
-    L += e + 1 - 3;
+    L += e + 2 - 3;
   }
 
   __device__ __forceinline__ void renorm() {}
