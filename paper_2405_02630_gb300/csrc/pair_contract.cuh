@@ -869,16 +869,20 @@ struct Engine<4, QSVM_FP32_SPLIT> {
   // with rho_0 = alpha_i conj(alpha_j), rho_1 = beta_i conj(beta_j); E'_s[p][pp] =
   // X_s[p][0] + X_s[p][1] conj(b[pp]) (b = (alpha_j, beta_j)): 24 complex MACs and two
   // phase products per site, and 16 re-splits (Y_1, X[.][1], E; Y_0 and X[.][0] only
-  // seed the next sum).  Grids: hi(rho) on 2^-kGridT, hi(E) on 2^-kGridE, hi(Y_1) on
-  // 2^-GG, hi(X[.][1]) on 2^-GX.  Exactness (|hi(alpha)|, |hi(rho)| <= 1.0004, E's
-  // components below 1/2 after renormalisation): hi(Y) sums on 2^-21 with partial sums
-  // <= 1.5; |Y| <= 1.42, so hi(X) = hi(Y_0) + hi(rho) hi(Y_1) sums on 2^-21 stay below
-  // 2.84; |X| <= 2.84, so hi(E') = hi(X[.][0]) + hi(X[.][1]) hi(conj b) sums on
-  // 2^-(GX + kGridT) = 2^-21 stay below 5.7 < 8 (< 2^24 units).
-  static constexpr int GG = kGridG, GX = 10;
-  static constexpr int kRenormEvery = 1;  // built into site()
+  // seed the next sum).  E is not rescaled every site: with U = 2^(e+1), e the frexp
+  // exponent of E's largest component, E's components are below U/2 and the hi parts of
+  // E, Y_1 and X[.][1] all sit on the grid U 2^-10 (one rounding constant per site, Cg),
+  // hi(rho) on 2^-kGridT.  Exactness in units of U (|hi(alpha)|, |hi(rho)| <= 1.0004):
+  // hi(Y) sums on U 2^-21 with partial sums <= 1.5 U; |Y| <= 1.42 U, so hi(X) = hi(Y_0) +
+  // hi(rho) hi(Y_1) sums on U 2^-21 stay below 2.84 U; |X| <= 2.84 U, so hi(E') =
+  // hi(X[.][0]) + hi(X[.][1]) hi(conj b) sums on U 2^-21 stay below 5.7 U (< 2^24 units).
+  // Every kRenormEvery sites (all threads at once) an exact power-of-two rescale, counted
+  // in L, brings e back to 0; a guard rescales at once if e leaves +-96 in between.
+  static constexpr int kRenormEvery = 8;
   using Rec = Record<4, QSVM_FP32_SPLIT>;
-  float2 Eh[2][2][2], El[2][2][2], Ef[2][2][2];  // Ef = fl(Eh + El)
+  float2 Eh[2][2][2], El[2][2][2];
+  float Cg;  // 1.5 * 2^(e + 14): adding and subtracting it rounds to the grid U 2^-10
+  int eE;    // e of the current environment
   int L;
 
   __device__ __forceinline__ void init() {
@@ -887,8 +891,10 @@ struct Engine<4, QSVM_FP32_SPLIT> {
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll
-        for (int r = 0; r < 2; ++r) Eh[c][q][r] = El[c][q][r] = Ef[c][q][r] = make_float2(0.f, 0.f);
-    Eh[0][0][0].x = Ef[0][0][0].x = 1.f;
+        for (int r = 0; r < 2; ++r) Eh[c][q][r] = El[c][q][r] = make_float2(0.f, 0.f);
+    Eh[0][0][0].x = 1.f;
+    eE = 1;  // E = e_0 e_0^T: largest component 1
+    Cg = grid_const(eE);
     L = 2;  // every site() counts -2 for the factors 1/2 of a and b; the virtual site has none
   }
 
@@ -913,10 +919,14 @@ struct Engine<4, QSVM_FP32_SPLIT> {
     ll = fma2(bc(wf.x), V.l, ll);
     ll = fma2(bc(wf.y), V.il, ll);
   }
-  template <int GS>
-  static __device__ __forceinline__ void ssplit(float2 hh, float2 ll, float2& xh, float2& xl, float2& xf) {
+  // 1.5 * 2^(e + 14) for the frexp exponent e (|e| <= 32 here)
+  static __device__ __forceinline__ float grid_const(int e) {
+    return __int_as_float(((127 + 14 + e) << 23) | 0x400000);
+  }
+  // re-split onto the grid of the rounding constant C
+  static __device__ __forceinline__ void ssplit(float2 hh, float2 ll, float C, float2& xh, float2& xl, float2& xf) {
     const float2 v = add2(hh, ll);
-    xh = grid_round2<GS>(v);
+    xh = add2(add2(v, bc(C)), bc(-C));
     xl = add2(fma2(xh, make_float2(-1.f, -1.f), hh), ll);  // (hh - xh) is exact
     xf = v;
   }
@@ -931,13 +941,13 @@ struct Engine<4, QSVM_FP32_SPLIT> {
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
           float2 hh = Eh[0][0][r], ll = El[0][0][r];
-          smac(hh, ll, Eh[0][1][r], El[0][1][r], Ef[0][1][r], p ? A1 : A0);
+          smac(hh, ll, Eh[0][1][r], El[0][1][r], add2(Eh[0][1][r], El[0][1][r]), p ? A1 : A0);
           Y0h[p][r] = hh;
           Y0l[p][r] = ll;
           hh = Eh[1][0][r];
           ll = El[1][0][r];
-          smac(hh, ll, Eh[1][1][r], El[1][1][r], Ef[1][1][r], p ? A1 : A0);
-          ssplit<GG>(hh, ll, Y1h[p][r], Y1l[p][r], Y1f[p][r]);
+          smac(hh, ll, Eh[1][1][r], El[1][1][r], add2(Eh[1][1][r], El[1][1][r]), p ? A1 : A0);
+          ssplit(hh, ll, Cg, Y1h[p][r], Y1l[p][r], Y1f[p][r]);
         }
     }
     SplitForm R[2];
@@ -958,7 +968,7 @@ struct Engine<4, QSVM_FP32_SPLIT> {
           float2 hh = Y0h[p][r], ll = Y0l[p][r];
           smac(hh, ll, Y1h[p][r], Y1l[p][r], Y1f[p][r], R[s]);
           if (r) {
-            ssplit<GX>(hh, ll, Xh[p][r], Xl[p][r], Xf[p][r]);
+            ssplit(hh, ll, Cg, Xh[p][r], Xl[p][r], Xf[p][r]);
           } else {  // seeds E'_s[p][.]
             Xh[p][r] = hh;
             Xl[p][r] = ll;
@@ -974,8 +984,8 @@ struct Engine<4, QSVM_FP32_SPLIT> {
           Nl[s][p][pp] = ll;
         }
     }
-    // renormalise by 2^-(e+1) (components below 1/2), apply the signs (-1)^{p+pp} of
-    // S E_1 S, re-split onto the E grid
+    // the new environment: its exponent sets this site's grid; an exact rescale keeps e
+    // within +-32; the signs (-1)^{p+pp} of S E_1 S are applied; re-split onto U 2^-10
     const float2 m1 = make_float2(-1.f, -1.f);
     float2 V[2][2][2];
 #pragma unroll
@@ -984,44 +994,62 @@ struct Engine<4, QSVM_FP32_SPLIT> {
       for (int p = 0; p < 2; ++p)
 #pragma unroll
         for (int r = 0; r < 2; ++r) V[s][p][r] = add2(Nh[s][p][r], Nl[s][p][r]);
-    const float m = max_abs<8>(reinterpret_cast<const float2(&)[8]>(V));
-    int e = 0;
-    if (m > 0.f && isfinite(m)) {
-      e = exp_of(m);
-      if (e < -120) {  // collapse to near zero: scale up in two exact steps
-        const float2 up = bc(pow2f(100));
+    float m = max_abs<8>(reinterpret_cast<const float2(&)[8]>(V));
+    int e = (m > 0.f && isfinite(m)) ? exp_of(m) : 0;
+    if (e > 96 || e < -96) {  // rare guard between the periodic rescales
+      const float2 sc = bc(pow2f(-e));
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < 2; ++s)
 #pragma unroll
-          for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 2; ++p)
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-              Nh[s][p][r] = mul2(Nh[s][p][r], up);
-              Nl[s][p][r] = mul2(Nl[s][p][r], up);
-              V[s][p][r] = mul2(V[s][p][r], up);
-            }
-        L -= 100;
-        e += 100;
-      }
+          for (int r = 0; r < 2; ++r) {
+            Nh[s][p][r] = mul2(Nh[s][p][r], sc);
+            Nl[s][p][r] = mul2(Nl[s][p][r], sc);
+            V[s][p][r] = mul2(V[s][p][r], sc);
+          }
+      L += e;
+      m = max_abs<8>(reinterpret_cast<const float2(&)[8]>(V));
+      e = (m > 0.f && isfinite(m)) ? exp_of(m) : 0;
     }
-    const float sc = pow2f(-(e + 1));
+    eE = e;
+    Cg = grid_const(e);
+    const float2 cp = bc(Cg), cm = bc(-Cg);
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
       for (int p = 0; p < 2; ++p)
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-          const float2 scs = bc((s == 1 && ((p + r) & 1)) ? -sc : sc);
-          const float2 f = mul2(V[s][p][r], scs);
-          const float2 h = grid_round2<kGridE>(f);
-          Eh[s][p][r] = h;
-          El[s][p][r] = fma2(Nl[s][p][r], scs, fma2(h, m1, mul2(Nh[s][p][r], scs)));
-          Ef[s][p][r] = f;
+          const float2 h = add2(add2(V[s][p][r], cp), cm);
+          const float2 l = add2(fma2(h, m1, Nh[s][p][r]), Nl[s][p][r]);  // (Nh - h) is exact
+          if (s == 1 && ((p + r) & 1)) {
+            Eh[s][p][r] = mul2(h, m1);
+            El[s][p][r] = mul2(l, m1);
+          } else {
+            Eh[s][p][r] = h;
+            El[s][p][r] = l;
+          }
         }
-    L += e + 1 - 2;
+    L -= 2;
   }
 
-  __device__ __forceinline__ void renorm() {}
+  // periodic rescale by 2^-e (exact; every thread of the warp at the same site)
+  __device__ __forceinline__ void renorm() {
+    const float2 sc = bc(pow2f(-eE));
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          Eh[s][p][r] = mul2(Eh[s][p][r], sc);
+          El[s][p][r] = mul2(El[s][p][r], sc);
+        }
+    L += eE;
+    eE = 0;
+    Cg = grid_const(0);
+  }
 
   // after the virtual site the amplitude is entry (0, 0) of block 0 (up to a phase)
   __device__ __forceinline__ void amplitude(double& re, double& im) const {
@@ -1449,7 +1477,10 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
         // two sites per iteration let the compiler start a site's shared loads
         // during the previous site's renormalisation (within the register budget)
 #pragma unroll 2
-        for (int s = 0; s < ns; ++s) eng.site(pa + s * Rec::kBytes, pb + s * Rec::kBytes);
+        for (int s = 0; s < ns; ++s) {
+          eng.site(pa + s * Rec::kBytes, pb + s * Rec::kBytes);
+          if (Eng::kRenormEvery > 1 && ((k0 + s + 1) % Eng::kRenormEvery) == 0) eng.renorm();
+        }
       } else {
 #pragma unroll 1
         for (int s = 0; s < ns; ++s) {
