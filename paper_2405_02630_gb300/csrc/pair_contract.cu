@@ -15,13 +15,12 @@ static const PipeShape kShapes[] = {{512, 4},  {1024, 3}, {512, 3},  {1024, 2}, 
                                     {2048, 3}, {512, 2},  {1152, 2}, {1440, 2}, {2304, 2}, {3456, 2}};
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 
-// Defaults from shape sweeps on one GB300 (n = 784 Grams): at reps = 2 (phase
-// form, N = 8192) split FP32 two stages of seven sites (553 ms; three stages of
-// two: 680 ms) and plain FP32 two stages of fifteen (150 ms); at reps = 3 the
-// four-thread split kernel two stages of three 640-byte phase-form sites (two
-// CTAs per SM; with 1088-byte block records two sites per chunk had been best).  FP64 is
-// insensitive.  Two stages keep two CTAs per SM and the longer chunks pay the
-// per-chunk wait and hand-off less often.
+// Defaults from shape sweeps on one GB300 (n = 784 Grams): split FP32 with 64-byte
+// gauged records, two stages of 22 sites at reps = 2 and of 32 sites at reps = 3
+// (each within 0.5 % of the best of the twelve shapes); plain FP32 two stages of
+// fifteen phase-form sites.  FP64 is insensitive (within 0.3 %).  Two stages keep
+// two CTAs per SM and the longer chunks pay the per-chunk wait and hand-off less
+// often.
 int default_shape(int chi, int prec) {
   if (chi == 4 && prec == QSVM_FP32_SPLIT) return 9;
   if (chi == 4 && prec == QSVM_FP32) return 9;

@@ -13,17 +13,21 @@
 // repetition's ZZ phase, so a_1s = r_s a_0s with r_0 = exp(2 i theta_{k-1}) and
 // r_1 = conj(r_0) (the record stores a_0s and r).  Hence
 //     E'_s = a_0s^T (E_0 + rho_s E_1) conj(b_0s),   rho_s = r_s(i) conj(r_s(j)),
-// chi^3/2 + chi^2/2 + 1 complex MACs per site instead of chi^3.  At reps = 2 the
-// site tensors are generated in registers from three unit phases per site (the
-// phase form, below): 33 complex MACs per site.
+// chi^3/2 + chi^2/2 + 1 complex MACs per site instead of chi^3 (the block form,
+// reps = 1).  Plain FP32 at reps = 2 generates the site tensors in registers from
+// three unit phases per site (the phase form, 33 complex MACs per site).  FP64 and
+// split FP32 at reps = 2 and 3 use the gauged form (a change of bond basis after
+// which a site is two phases alpha, beta; see Record<4, QSVM_FP32_SPLIT>): 26
+// complex MACs per site at reps = 2, 160 at reps = 3, plus one virtual site.
 //
 // One CTA owns a TI x TI tile of pairs, one thread per pair, E in registers for
 // all n sites.  The tile's 2*TI points stream their site records through shared
 // memory in chunks of S sites: one thread issues one bulk (TMA) copy per point
 // and chunk, completion is tracked by an mbarrier per stage.
 //
-// Renormalisation: E is scaled by an exact power of two 2^-e (max |component| of
-// E into [0.5, 1)) and e is accumulated in an integer, so the scale is exact.
+// Renormalisation: E is scaled by an exact power of two and the exponent is
+// accumulated in an integer, so the scale is exact (the split reps = 2 engine lets
+// its grids follow E's exponent and rescales every few sites instead).
 #pragma once
 
 #include <math.h>
@@ -515,7 +519,7 @@ struct Engine<CHI, QSVM_FP32_SPLIT> {
   }
 };
 
-// ------------------------------------------------ phase form (reps = 2) ----
+// --------------------------------------- phase form (reps = 2, plain FP32) ----
 // The row point's blocks, unscaled (their factors 1/2 go to the log scale:
 // L -= 2 per site), with V0 = T^2, V1 = P^2, V2 = P^2 T^2 (rows q, columns p):
 //   a_00 = [[V2, 1], [V1, V0]],   a_01 = [[1, -conj(V2)], [conj(V0), -conj(V1)]].
@@ -850,12 +854,10 @@ struct Engine<4, QSVM_FP32> {
   }
 };
 
-// Split FP32 in phase form.  Grids as in the block form except that the phases
-// have modulus 1 instead of 1/2, which the two intermediate grids absorb: G on
-// 2^-9 (|G| <= 1 + sqrt(2); X = V G sums 4 products <= 4 * 2^11 * 1236.5 < 1.02e7
-// units of 2^-20) and X on 2^-8 (|X| <= 4 sqrt(2); E' sums 4 products
-// <= 4 * 2^11 * 1448.7 < 1.19e7 units of 2^-19); the identity entries add an
-// operand already on the coarser grid.  Both stay below 2^24 = 1.68e7.
+// ------------------------------------------- gauged form, split FP32 -----
+// A split value's packed forms as read from a gauged-form record or formed for rho:
+// hi (h, ih) and lo (l, il), each as the pair (V, iV) (row side, a-form) or
+// (conj V, i conj V) (column side, b-form).
 struct SplitForm {
   float2 h, ih, l, il;
 };

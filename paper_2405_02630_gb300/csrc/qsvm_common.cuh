@@ -17,10 +17,12 @@ namespace qsvm {
 constexpr double kPi = 3.14159265358979323846;
 
 // Binary grids of the split-FP32 format.  Tensor and phase hi parts sit on
-// 2^-kGridT; environment hi parts on 2^-kGridE after renormalisation to
-// max |.| < 1; the mixed environment G = E_0 + rho E_1 on 2^-kGridG; the
-// intermediate (a^T G) on 2^-grid_x(chi).  The exactness argument (every hi*hi
-// partial sum stays below 2^24 grid units) is spelled out in pair_contract.cuh.
+// 2^-kGridT in every form.  The block-form engine (reps = 1) keeps environment hi
+// parts on 2^-kGridE after renormalisation to max |.| < 1, the mixed environment
+// G = E_0 + rho E_1 on 2^-kGridG and the intermediate (a^T G) on 2^-grid_x(chi);
+// the gauged engines (reps = 2, 3) choose their own grids.  The exactness argument
+// (every hi*hi partial sum stays below 2^24 grid units) is spelled out with each
+// engine in pair_contract.cuh.
 constexpr int kGridT = 11;
 constexpr int kGridE = 10;
 constexpr int kGridG = 10;
