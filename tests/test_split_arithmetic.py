@@ -1,0 +1,165 @@
+"""CPU model of the split-FP32 arithmetic of the reps = 2 pair kernel (gauged form).
+
+The kernel's operation order is replayed in numpy on float32-representable float64
+arrays.  Every hi*hi product and hi sum that the kernel relies on being exact is
+checked to be a float32 value, and every other FMA or add is rounded to float32 as
+the kernel does.  Per site:
+    rho_s = (alpha_i, beta_i)[s] conj(...)_j, re-split onto 2^-11;
+    Y_c[p][r] = E_c[0][r] + a[p] E_c[1][r], Y_1 re-split onto U 2^-10;
+    X_s = Y_0 + rho_s Y_1, X[.][1] re-split onto U 2^-10, X[.][0] kept unsplit;
+    E'_s[p][pp] = X_s[p][0] + conj(b[pp]) X_s[p][1];
+then E' is re-split onto U 2^-10 with U = 2^(e+1) from its largest component, and the
+signs of S E_1 S are applied.  This pins the exactness argument of the grids (no
+inexact hi operation at n = 784 on near-duplicate and random pairs) and shows that the
+arithmetic itself, before any GPU is involved, meets |dK| <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+from paper_2405_02630_gb300 import inputs
+
+F = np.float32
+
+
+def f32(a):
+    return np.asarray(a, np.float64).astype(F).astype(np.float64)
+
+
+class _Model:
+    def __init__(self):
+        self.inexact = 0
+
+    def exact(self, v):
+        r = f32(v)
+        self.inexact += int(np.sum(r != v))
+        return r
+
+    @staticmethod
+    def fma(a, b, c):
+        return f32(a * b + c)
+
+    @staticmethod
+    def rnd(v, grid):  # nearest multiple of grid, ties to even (the kernel's (v + C) - C)
+        return np.round(v / grid) * grid
+
+
+def _gauged(X):
+    P, n = X.shape
+    th = np.zeros((P, n + 1))
+    th[:, 1:n] = (np.pi - X[:, :-1]) * (np.pi - X[:, 1:])
+    xp = np.concatenate([np.zeros((P, 1)), X], axis=1)
+    tp = np.concatenate([np.zeros((P, 1)), th[:, :n]], axis=1)
+    out = []
+    for z in (np.exp(2j * (xp + tp + th)), np.exp(2j * (xp + tp - th))):
+        h = np.round(z * 2048) / 2048  # hi on 2^-11 (re and im separately)
+        h = np.round(z.real * 2048) / 2048 + 1j * np.round(z.imag * 2048) / 2048
+        out.append((h, f32(z.real - h.real) + 1j * f32(z.imag - h.imag)))
+    return out
+
+
+def _contract(Xa, Xb):
+    """K for pairs (Xa[k], Xb[k]) in the kernel's split arithmetic (complex128 arrays whose
+    real and imaginary parts are float32 values)."""
+    M = _Model()
+    (ai, bi), (aj, bj) = _gauged(Xa), _gauged(Xb)
+    P, n1 = ai[0].shape
+    cr = lambda z: (z.real, z.imag)
+
+    def smac(hh, ll, wh, wl, wf, Vh, Vl, conj_v):
+        # hh += wh V (exact), ll += wl V_h + wf V_l; V given by hi and lo (conj on the column side)
+        vh = np.conj(Vh) if conj_v else Vh
+        vl = np.conj(Vl) if conj_v else Vl
+        hr = M.exact(M.exact(hh.real + wh.real * vh.real) - wh.imag * vh.imag)
+        hi = M.exact(M.exact(hh.imag + wh.real * vh.imag) + wh.imag * vh.real)
+        lr = M.fma(wf.imag, -vl.imag, M.fma(wf.real, vl.real, M.fma(wl.imag, -vh.imag, M.fma(wl.real, vh.real, ll.real))))
+        li = M.fma(wf.imag, vl.real, M.fma(wf.real, vl.imag, M.fma(wl.imag, vh.real, M.fma(wl.real, vh.imag, ll.imag))))
+        return hr + 1j * hi, lr + 1j * li
+
+    def ssplit(hh, ll, grid):
+        v = f32(hh.real + ll.real) + 1j * f32(hh.imag + ll.imag)
+        xh = M.rnd(v.real, grid) + 1j * M.rnd(v.imag, grid)
+        xl = f32(M.exact(hh.real - xh.real) + ll.real) + 1j * f32(M.exact(hh.imag - xh.imag) + ll.imag)
+        return xh, xl, v
+
+    z = np.zeros(P, complex)
+    Eh = np.zeros((2, 2, 2, P), complex)
+    El = np.zeros((2, 2, 2, P), complex)
+    Eh[0, 0, 0] = 1.0
+    U = 4.0  # 2^(e+1) with e = 1 for E = e_0 e_0^T
+    L = np.full(P, 2.0)
+    for k in range(n1):
+        A = [(ai[0][:, k], ai[1][:, k]), (bi[0][:, k], bi[1][:, k])]
+        B = [(aj[0][:, k], aj[1][:, k]), (bj[0][:, k], bj[1][:, k])]
+        R = []
+        for s in range(2):  # rho_s = u conj(w): hi products exact, lo by an FMA chain, re-split onto 2^-11
+            (uh, ul), (wh, wl) = A[s], B[s]
+            hr = M.exact(uh.real * wh.real + uh.imag * wh.imag)
+            hi = M.exact(uh.imag * wh.real - uh.real * wh.imag)
+            fr, fi = f32(uh.real + ul.real), f32(uh.imag + ul.imag)
+            lr = M.fma(ul.real, wh.real, M.fma(ul.imag, wh.imag, M.fma(fr, wl.real, f32(fi * wl.imag))))
+            li = M.fma(ul.real, -wh.imag, M.fma(ul.imag, wh.real, M.fma(fr, -wl.imag, f32(fi * wl.real))))
+            R.append(ssplit(hr + 1j * hi, lr + 1j * li, 2.0 ** -11)[:2])
+        Y0, Y1 = {}, {}
+        for r in range(2):
+            for p in range(2):
+                for c in range(2):
+                    wf = f32(Eh[c, 1, r].real + El[c, 1, r].real) + 1j * f32(Eh[c, 1, r].imag + El[c, 1, r].imag)
+                    hh, ll = smac(Eh[c, 0, r], El[c, 0, r], Eh[c, 1, r], El[c, 1, r], wf, *A[p], False)
+                    if c:
+                        Y1[p, r] = ssplit(hh, ll, U * 2.0 ** -10)
+                    else:
+                        Y0[p, r] = (hh, ll)
+        Nh = np.zeros((2, 2, 2, P), complex)
+        Nl = np.zeros((2, 2, 2, P), complex)
+        for s in range(2):
+            Xs = {}
+            for p in range(2):
+                for r in range(2):
+                    rh, rl = R[s]
+                    rf = f32(rh.real + rl.real) + 1j * f32(rh.imag + rl.imag)
+                    y1h, y1l, y1f = Y1[p, r]
+                    hh, ll = smac(Y0[p, r][0], Y0[p, r][1], y1h, y1l, y1f, rh, rl, False)
+                    Xs[p, r] = ssplit(hh, ll, U * 2.0 ** -10) if r else (hh, ll, None)
+            for p in range(2):
+                for pp in range(2):
+                    xh, xl, xf = Xs[p, 1]
+                    Nh[s, p, pp], Nl[s, p, pp] = smac(Xs[p, 0][0], Xs[p, 0][1], xh, xl, xf, *B[pp], True)
+        V = f32(Nh.real + Nl.real) + 1j * f32(Nh.imag + Nl.imag)
+        m = np.max(np.maximum(np.abs(V.real), np.abs(V.imag)).reshape(-1, P), axis=0)
+        e = np.frexp(m)[1]
+        U = np.ldexp(1.0, e + 1)
+        for s in range(2):
+            for p in range(2):
+                for pp in range(2):
+                    h = M.rnd(V[s, p, pp].real, U * 2.0 ** -10) + 1j * M.rnd(V[s, p, pp].imag, U * 2.0 ** -10)
+                    l = (f32(M.exact(Nh[s, p, pp].real - h.real) + Nl[s, p, pp].real)
+                         + 1j * f32(M.exact(Nh[s, p, pp].imag - h.imag) + Nl[s, p, pp].imag))
+                    sg = -1.0 if (s == 1 and (p + pp) % 2) else 1.0
+                    Eh[s, p, pp], El[s, p, pp] = sg * h, sg * l
+        # an exact rescale to e = 0 (the kernel does it every 8 sites; values are unchanged)
+        Eh = Eh * np.ldexp(1.0, -e)
+        El = El * np.ldexp(1.0, -e)
+        L = L + e - 2
+        U = 2.0
+    amp = (Eh[0, 0, 0] + El[0, 0, 0])
+    return np.abs(amp) ** 2 * 2.0 ** (2 * L), M.inexact
+
+
+@pytest.fixture(scope="module")
+def pairs(oracle):
+    base = inputs.mnist_like_features(24, 784, 21)
+    pert = inputs.near_duplicates(base, 22)
+    ra, rb = inputs.mnist_like_features(24, 784, 5), inputs.mnist_like_features(24, 784, 6)
+    idx = np.arange(24)
+    K1, _ = oracle.mps_pairs(base, pert, idx, idx, 2)
+    K2, _ = oracle.mps_pairs(ra, rb, idx, idx, 2)
+    return (base, pert, K1), (ra, rb, K2)
+
+
+def test_split_arithmetic_is_exact_and_accurate(pairs):
+    (base, pert, K1), (ra, rb, K2) = pairs
+    k1, bad1 = _contract(base, pert)
+    k2, bad2 = _contract(ra, rb)
+    assert bad1 == 0 and bad2 == 0, f"inexact hi operations: {bad1}, {bad2}"
+    assert np.max(np.abs(k1 - K1)) <= 3e-8  # near duplicates, K up to 0.9999
+    assert K2.max() < 1e-150 and np.max(np.abs(np.log(k2 / K2))) <= 5e-6  # tiny K: relative accuracy
