@@ -51,8 +51,7 @@ def _gauged(X):
     tp = np.concatenate([np.zeros((P, 1)), th[:, :n]], axis=1)
     out = []
     for z in (np.exp(2j * (xp + tp + th)), np.exp(2j * (xp + tp - th))):
-        h = np.round(z * 2048) / 2048  # hi on 2^-11 (re and im separately)
-        h = np.round(z.real * 2048) / 2048 + 1j * np.round(z.imag * 2048) / 2048
+        h = np.round(z.real * 2048) / 2048 + 1j * np.round(z.imag * 2048) / 2048  # hi on 2^-11
         out.append((h, f32(z.real - h.real) + 1j * f32(z.imag - h.imag)))
     return out
 
@@ -63,7 +62,6 @@ def _contract(Xa, Xb):
     M = _Model()
     (ai, bi), (aj, bj) = _gauged(Xa), _gauged(Xb)
     P, n1 = ai[0].shape
-    cr = lambda z: (z.real, z.imag)
 
     def smac(hh, ll, wh, wl, wf, Vh, Vl, conj_v):
         # hh += wh V (exact), ll += wl V_h + wf V_l; V given by hi and lo (conj on the column side)
