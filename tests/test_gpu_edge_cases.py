@@ -62,3 +62,26 @@ def test_ragged_cross_n784(q, oracle, prec):
     K = K.cpu().numpy()
     assert np.max(np.abs(K - Ko)) <= TOL[prec]
     assert abs(K[5, 7] - 1) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
+def test_long_chain_reps3_n2048(q, oracle, prec):
+    """reps = 3 over 2048 sites: K underflows off the diagonal while ln K stays exact."""
+    X = inputs.mnist_like_features(6, 2048, 23)
+    X[4] = X[1]
+    K, LK = q.gram(torch.from_numpy(X).cuda(), 3, prec, logK=True)
+    Ko, LKo = oracle.mps_gram(X, 3)
+    K, L = K.cpu().numpy(), LK.cpu().numpy()
+    assert np.max(np.abs(K - Ko)) <= TOL[prec]
+    assert abs(K[1, 4] - 1.0) <= TOL[prec] and np.all(np.isfinite(L))
+    assert np.max(np.abs(L - LKo)) <= (1e-8 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
+@pytest.mark.parametrize("reps", [1, 2, 3])
+def test_wide_angle_range(q, oracle, prec, reps):
+    """Features anywhere in [-3 pi, 3 pi] (the map takes any angle)."""
+    X = np.random.default_rng(40 + reps).uniform(-3 * np.pi, 3 * np.pi, (9, 33))
+    K, _ = q.gram(torch.from_numpy(X).cuda(), reps, prec)
+    Ko, _ = oracle.mps_gram(X, reps)
+    assert np.max(np.abs(K.cpu().numpy() - Ko)) <= TOL[prec]
