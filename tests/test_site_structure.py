@@ -192,3 +192,37 @@ def test_reps3_gauged_form_is_a_kronecker_square(oracle):
             assert np.max(np.abs(blk[0] - kron)) <= 1e-13, (k, s)
             r = alpha[k] if s == 0 else beta[k]
             assert np.max(np.abs(blk[1] - r * S @ kron)) <= 1e-13, (k, s)
+
+
+@pytest.mark.parametrize("n,seed", [(2, 361), (6, 362), (9, 363)])
+def test_reps3_gauged_contraction(oracle, n, seed):
+    """The reps = 3 update of the four-thread engine: with the row signs T = diag(1, 1, 1, -1)
+    and S = diag(1, 1, -1, -1) folded into the stored environment Ev_c = T S^c E_c S^c T,
+    Y_c = (M_i x M_i)^T Ev_c in two 2 x 2 stages, X_s = Y_0 + rho_s Y_1, E'_s = X_s
+    conj(M_j x M_j) in two stages; after the virtual site K = |E_0[0][0]|^2 2^(-6n)."""
+    X = np.concatenate([inputs.uniform_features(3, n, seed), inputs.mnist_like_features(1, n, seed)])
+    T = np.array([1.0, 1.0, 1.0, -1.0])
+    Sg = np.array([1.0, 1.0, -1.0, -1.0])
+
+    def rows(Mv, E):  # (M x M)^T applied to the row index q = q1 + 2 q2 of E, as two stages
+        a, b = Mv
+        Z = np.stack([E[0] + a * E[1], E[0] + b * E[1], E[2] + a * E[3], E[2] + b * E[3]])
+        return np.stack([Z[0] + a * Z[2], Z[1] + a * Z[3], Z[0] + b * Z[2], Z[1] + b * Z[3]])
+
+    for i, j in ((0, 1), (2, 3), (1, 1)):
+        (ai, bi), (aj, bj) = _gauged_alpha_beta(X[i]), _gauged_alpha_beta(X[j])
+        Ev = [np.zeros((4, 4), complex), np.zeros((4, 4), complex)]
+        Ev[0][0, 0] = 1.0
+        for k in range(n + 1):
+            Y = [rows((ai[k], bi[k]), Ev[c]) for c in range(2)]
+            rho = [ai[k] * np.conj(aj[k]), bi[k] * np.conj(bj[k])]
+            new = []
+            for s in range(2):
+                Xs = Y[0] + rho[s] * Y[1]
+                Ep = rows((np.conj(aj[k]), np.conj(bj[k])), Xs.T).T  # columns, conjugated M_j
+                sg = np.outer(T, T) * (np.outer(Sg, Sg) if s else 1.0)
+                new.append(sg * Ep)
+            Ev = new
+        K = abs(Ev[0][0, 0]) ** 2 * 2.0 ** (-6 * n)
+        Ko, _ = oracle.sv_kernel_pair(X[i], X[j], 3)
+        assert abs(K - Ko) <= 1e-13 and abs(K / Ko - 1) <= 1e-11, (n, i, j, K, Ko)
