@@ -364,6 +364,9 @@ def run_ours(args):
                 "algorithmic_flops_per_entry": 8 * cm,
                 "block_sparse_flops_per_entry": 8 * structured_cmacs_per_entry(n, reps),
                 "dense_equiv_flops_per_entry": 8 * dense_cmacs_per_entry(n, reps),
+                # the same launch counted in the dense per-entry work (minimal bonds, no
+                # factorization): above the peak because the kernel's form needs less work
+                "dense_equiv_tflops": 8.0 * dense_cmacs_per_entry(n, reps) * pairs_rank / (kms * 1e-3) / 1e12,
                 "fma_pipe_frac": fma_frac}
 
     line = {
