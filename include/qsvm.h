@@ -185,7 +185,10 @@ int32_t qsvm_kernel_cross(const void* mps_a, int64_t n_a, const void* mps_b, int
  *          caller: X, the MPS and K (and logK) are staged there.
  * Stream-ordered on `stream` (the helper streams are joined back into it): K and logK
  * are complete once `stream` has reached this point; the call itself does not
- * wait.  Results are bit-identical to qsvm_build_mps + qsvm_kernel_gram.
+ * wait.  The helper streams are created and released by each call, so the call is
+ * not meant for CUDA-graph capture (capture qsvm_build_mps + qsvm_kernel_gram on
+ * device buffers instead), and one ws serves one call at a time.  Results are
+ * bit-identical to qsvm_build_mps + qsvm_kernel_gram.
  * Errors: as qsvm_kernel_gram, and QSVM_ERR_ARG for a missing or short ws. */
 size_t qsvm_gram_host_workspace_bytes(int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
                                       int32_t with_logk);
