@@ -459,24 +459,35 @@ def run_ours(args):
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: qsvm_gram_host copies pinned host X
         # to the device, builds, computes the Gram and copies K back to pinned host memory
-        # (row bands overlapped with the remaining launches).  A rank of a sharded run
-        # (world > 1) computes its tile range on device buffers and copies its rows.
+        # (row bands overlapped with the remaining launches); qsvm_cross_host does the same
+        # for the test x train kernel.  A rank of a sharded run (world > 1) computes its
+        # tile range on device buffers and copies the whole matrices.
         Xh = torch.from_numpy(X).pin_memory()
         Kh = torch.empty((N, N), dtype=torch.float64).pin_memory()
+        Xteh = torch.from_numpy(Xte).pin_memory() if Nte else None
+        Kxh = torch.empty((Nte, N), dtype=torch.float64).pin_memory() if Nte else None
         ws_h = torch.empty(qsvm.qsvm_gram_host_workspace_bytes(N, n, reps, P), dtype=torch.uint8, device=dev) \
             if world == 1 else None
+        ws_x = torch.empty(qsvm.qsvm_cross_host_workspace_bytes(Nte, N, n, reps, P), dtype=torch.uint8,
+                           device=dev) if world == 1 and Nte else None
         e2e_ms = []
         for it in range(max(2, min(args.steps, 3)) + 1):
             flush.fill_(1.0)
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            if world == 1 and not Nte:
+            if world == 1:
                 qsvm.gram_host(Xh, reps, P, K=Kh, ws=ws_h, stream=stream)
+                if Nte:
+                    qsvm.cross_host(Xteh, Xh, reps, P, K=Kxh, ws=ws_x, stream=stream)
             else:
                 Xd.copy_(Xh, non_blocking=True)
+                if Nte:
+                    Xted.copy_(Xteh, non_blocking=True)
                 step()
                 Kh.copy_(K, non_blocking=True)
+                if Nte:
+                    Kxh.copy_(Kx, non_blocking=True)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             if it > 0:
@@ -487,7 +498,8 @@ def run_ours(args):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             em = float(t[0])
         line["e2e"] = {"value": total_pairs / (em * 1e-3), "unit": "entries/s",
-                       "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(N * N * 8)}
+                       "h2d_bytes_per_step": int(X.nbytes) + (int(Xte.nbytes) if Nte else 0),
+                       "d2h_bytes_per_step": int((N + Nte) * N * 8)}
 
     if rank == 0:
         print(json.dumps(line), flush=True)

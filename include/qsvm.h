@@ -195,6 +195,23 @@ size_t qsvm_gram_host_workspace_bytes(int64_t n_points, int32_t n_qubits, int32_
 int32_t qsvm_gram_host(const double* X, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
                        double* K, int64_t ldk, double* logK, int64_t ldl, void* ws, size_t ws_bytes, void* stream);
 
+/* qsvm_cross_host -- the test x train kernel of host data, end to end: X_a (HOST,
+ * n_a x n_qubits float64, the test points) and X_b (HOST, n_b x n_qubits, the train
+ * points) are copied to the device and their MPS built; the kernel (K[i*ldk + j] as in
+ * qsvm_kernel_cross, HOST float64, ldk >= n_b; logK HOST or NULL, ldl >= n_b) runs in
+ * about eight launches of whole tile rows, and each launch's rows are copied to the
+ * host on a second stream while the next launch computes.
+ *   ws  device scratch of qsvm_cross_host_workspace_bytes(n_a, n_b, n_qubits, reps,
+ *       precision, logK != NULL) bytes, 256-byte aligned, owned by the caller.
+ * Stream-ordered on `stream` as qsvm_gram_host (the same capture and workspace
+ * caveats).  Results are bit-identical to qsvm_build_mps + qsvm_kernel_cross.
+ * Errors: as qsvm_kernel_cross, and QSVM_ERR_ARG for a missing or short ws. */
+size_t qsvm_cross_host_workspace_bytes(int64_t n_a, int64_t n_b, int32_t n_qubits, int32_t reps, int32_t precision,
+                                       int32_t with_logk);
+int32_t qsvm_cross_host(const double* X_a, int64_t n_a, const double* X_b, int64_t n_b, int32_t n_qubits,
+                        int32_t reps, int32_t precision, double* K, int64_t ldk, double* logK, int64_t ldl, void* ws,
+                        size_t ws_bytes, void* stream);
+
 /* ---- sharding the symmetric Gram over independent workers ----------------
  * The upper-triangle pair tiles of a Gram are independent (Sec. 5: pairs are
  * distributed evenly over GPUs and the results gathered).  A tile is a

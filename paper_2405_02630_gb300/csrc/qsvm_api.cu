@@ -435,6 +435,85 @@ int32_t qsvm_gram_host(const double* X, int64_t n_points, int32_t n_qubits, int3
   return QSVM_OK;
 }
 
+size_t qsvm_cross_host_workspace_bytes(int64_t n_a, int64_t n_b, int32_t n_qubits, int32_t reps, int32_t precision,
+                                       int32_t with_logk) {
+  if (n_a < 1 || n_b < 1 || n_qubits < 2) return 0;
+  const size_t ma = qsvm_mps_bytes(n_qubits, reps, n_a, precision), mb = qsvm_mps_bytes(n_qubits, reps, n_b, precision);
+  if (ma == 0 || mb == 0) return 0;
+  const size_t k = align256((size_t)n_a * (size_t)n_b * sizeof(double));
+  return align256((size_t)(n_a + n_b) * (size_t)n_qubits * sizeof(double)) + align256(ma) + align256(mb) +
+         k * (with_logk ? 2 : 1);
+}
+
+int32_t qsvm_cross_host(const double* X_a, int64_t n_a, const double* X_b, int64_t n_b, int32_t n_qubits,
+                        int32_t reps, int32_t precision, double* K, int64_t ldk, double* logK, int64_t ldl, void* ws,
+                        size_t ws_bytes, void* stream) {
+  int32_t rc = check_common(n_qubits, reps, precision);
+  if (rc) return rc;
+  if (n_a < 1 || n_b < 1) return fail(QSVM_ERR_ARG, "n_a=%lld, n_b=%lld must be >= 1", (long long)n_a, (long long)n_b);
+  if (!X_a || !X_b || !K) return fail(QSVM_ERR_ARG, "X_a, X_b and K must be non-null host pointers");
+  if (ldk < n_b) return fail(QSVM_ERR_ARG, "ldk=%lld < n_b=%lld", (long long)ldk, (long long)n_b);
+  if (logK && ldl < n_b) return fail(QSVM_ERR_ARG, "ldl=%lld < n_b=%lld", (long long)ldl, (long long)n_b);
+  const size_t need = qsvm_cross_host_workspace_bytes(n_a, n_b, n_qubits, reps, precision, logK != nullptr);
+  if (!ws || !aligned(ws, 256)) return fail(QSVM_ERR_ARG, "ws must be a non-null 256-byte aligned device pointer");
+  if (ws_bytes < need) return fail(QSVM_ERR_ARG, "ws_bytes=%zu < required %zu", ws_bytes, need);
+  uint8_t* base = static_cast<uint8_t*>(ws);
+  double* dXa = reinterpret_cast<double*>(base);
+  double* dXb = dXa + (size_t)n_a * (size_t)n_qubits;
+  base += align256((size_t)(n_a + n_b) * (size_t)n_qubits * sizeof(double));
+  const size_t ma = qsvm_mps_bytes(n_qubits, reps, n_a, precision), mb = qsvm_mps_bytes(n_qubits, reps, n_b, precision);
+  uint8_t* dMa = base;
+  base += align256(ma);
+  uint8_t* dMb = base;
+  base += align256(mb);
+  double* dK = reinterpret_cast<double*>(base);
+  double* dL = logK ? reinterpret_cast<double*>(base + align256((size_t)n_a * (size_t)n_b * sizeof(double))) : nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(dXa, X_a, (size_t)n_a * (size_t)n_qubits * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dXb, X_b, (size_t)n_b * (size_t)n_qubits * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy of X_a, X_b to the device");
+  rc = qsvm_build_mps(dXa, n_a, n_qubits, reps, precision, dMa, ma, stream);
+  if (!rc) rc = qsvm_build_mps(dXb, n_b, n_qubits, reps, precision, dMb, mb, stream);
+  if (rc) return rc;
+
+  // Row chunks of whole tile rows: the rows of a chunk are final when its launch
+  // completes, and a copy stream takes them to the host while the next one computes.
+  constexpr int kChunks = 8;
+  const int tdim = pair_tile_dim(1 << reps, precision);
+  const int64_t Ta = tiles_per_side(n_a, tdim);
+  const int64_t rows_per_chunk = ((Ta + kChunks - 1) / kChunks) * tdim;
+  const size_t point_bytes = qsvm_mps_point_bytes(n_qubits, reps, precision);
+  cudaStream_t xs = nullptr;
+  cudaEvent_t ev[kChunks + 1] = {};
+  e = cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking);
+  for (int c = 0; e == cudaSuccess && c <= kChunks; ++c) e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming);
+  for (int c = 0; e == cudaSuccess && rc == QSVM_OK && c < kChunks; ++c) {
+    const int64_t r0 = c * rows_per_chunk, r1 = std::min<int64_t>(n_a, r0 + rows_per_chunk);
+    if (r0 >= r1) break;
+    rc = qsvm_kernel_cross(dMa + (size_t)r0 * point_bytes, r1 - r0, dMb, n_b, n_qubits, reps, precision,
+                           dK + r0 * n_b, n_b, dL ? dL + r0 * n_b : nullptr, n_b, stream);
+    if (rc) break;
+    e = cudaEventRecord(ev[c], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, ev[c], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(K + r0 * ldk, (size_t)ldk * sizeof(double), dK + r0 * n_b, (size_t)n_b * sizeof(double),
+                            (size_t)n_b * sizeof(double), (size_t)(r1 - r0), cudaMemcpyDeviceToHost, xs);
+    if (e == cudaSuccess && logK)
+      e = cudaMemcpy2DAsync(logK + r0 * ldl, (size_t)ldl * sizeof(double), dL + r0 * n_b, (size_t)n_b * sizeof(double),
+                            (size_t)n_b * sizeof(double), (size_t)(r1 - r0), cudaMemcpyDeviceToHost, xs);
+  }
+  cudaError_t e2 = (xs && ev[kChunks]) ? cudaEventRecord(ev[kChunks], xs) : cudaSuccess;
+  if (xs && ev[kChunks] && e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, ev[kChunks], 0);
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  if (xs) cudaStreamDestroy(xs);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "chunked copy of the cross kernel to the host");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "joining the copy stream");
+  return QSVM_OK;
+}
+
 size_t qsvm_batch_workspace_bytes(int32_t n_jobs) { return n_jobs < 1 ? 0 : ws_total(n_jobs); }
 
 int32_t qsvm_kernel_batch(const qsvm_job* jobs, int32_t n_jobs, int32_t reps, int32_t precision, void* ws,

@@ -62,6 +62,8 @@ _SIGS = {
     "qsvm_kernel_cross": (_i32, [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _dp, _i64, _dp, _i64, _vp]),
     "qsvm_gram_host_workspace_bytes": (_sz, [_i64, _i32, _i32, _i32, _i32]),
     "qsvm_gram_host": (_i32, [_dp, _i64, _i32, _i32, _i32, _dp, _i64, _dp, _i64, _vp, _sz, _vp]),
+    "qsvm_cross_host_workspace_bytes": (_sz, [_i64, _i64, _i32, _i32, _i32, _i32]),
+    "qsvm_cross_host": (_i32, [_dp, _i64, _dp, _i64, _i32, _i32, _i32, _dp, _i64, _dp, _i64, _vp, _sz, _vp]),
     "qsvm_gram_tile_dim": (_i32, [_i32, _i32]),
     "qsvm_gram_num_tiles": (_i64, [_i64, _i32, _i32]),
     "qsvm_gram_partition": (_i32, [_i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
@@ -405,6 +407,32 @@ def gram_host(X, reps: int, precision, K=None, logK=False, ws=None, stream=None)
         ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     _check(lib().qsvm_gram_host(_ptr(X), N, n, reps, _prec(precision), _ptr(K), K.stride(0), _ptr(L),
                                 L.stride(0) if L is not None else 0, _ptr(ws), ws.numel(), _stream(stream)))
+    return K, L
+
+
+def qsvm_cross_host_workspace_bytes(n_a: int, n_b: int, n_qubits: int, reps: int, precision,
+                                    with_logk: bool = False) -> int:
+    return int(lib().qsvm_cross_host_workspace_bytes(n_a, n_b, n_qubits, reps, _prec(precision), int(bool(with_logk))))
+
+
+def cross_host(X_test, X_train, reps: int, precision, K=None, logK=False, ws=None, stream=None):
+    """Test x train kernel of host data through qsvm_cross_host (contiguous CPU float64
+    inputs; page-locked outputs allocated if not given).  Returns (K, logK or None), complete
+    once `stream` is synchronised."""
+    import torch
+    for X in (X_test, X_train):
+        if X.device.type != "cpu" or X.dtype != torch.float64 or not X.is_contiguous():
+            raise ValueError("X_test and X_train must be contiguous CPU float64 tensors")
+    na, n = X_test.shape
+    nb = X_train.shape[0]
+    if K is None:
+        K = torch.empty((na, nb), dtype=torch.float64, pin_memory=True)
+    L = torch.empty((na, nb), dtype=torch.float64, pin_memory=True) if logK is True else (logK or None)
+    need = qsvm_cross_host_workspace_bytes(na, nb, n, reps, precision, L is not None)
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    _check(lib().qsvm_cross_host(_ptr(X_test), na, _ptr(X_train), nb, n, reps, _prec(precision), _ptr(K), K.stride(0),
+                                 _ptr(L), L.stride(0) if L is not None else 0, _ptr(ws), ws.numel(), _stream(stream)))
     return K, L
 
 

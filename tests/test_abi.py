@@ -232,3 +232,36 @@ def test_gram_host_arguments():
     assert call(wsb=need - 1) == qsvm.QSVM_ERR_ARG
     assert call(N=0) == qsvm.QSVM_ERR_ARG
     assert call(reps=4) == qsvm.QSVM_ERR_CHI
+
+
+def test_cross_host_arguments():
+    """qsvm_cross_host checks its arguments on the host before any copy or launch."""
+    import ctypes
+    L = qsvm.lib()
+    v = lambda n: ctypes.c_void_p(256 * n)
+    Na, Nb, n = 40, 100, 24
+    a256 = lambda b: (b + 255) // 256 * 256
+    need = qsvm.qsvm_cross_host_workspace_bytes(Na, Nb, n, 2, "fp32_split")
+    assert need == (a256((Na + Nb) * n * 8) + a256(qsvm.qsvm_mps_bytes(n, 2, Na, "fp32_split"))
+                    + a256(qsvm.qsvm_mps_bytes(n, 2, Nb, "fp32_split")) + a256(Na * Nb * 8))
+    assert qsvm.qsvm_cross_host_workspace_bytes(Na, Nb, n, 2, "fp32_split", True) == need + a256(Na * Nb * 8)
+    assert qsvm.qsvm_cross_host_workspace_bytes(0, Nb, n, 2, "fp64") == 0
+    assert qsvm.qsvm_cross_host_workspace_bytes(Na, 0, n, 2, "fp64") == 0
+    assert qsvm.qsvm_cross_host_workspace_bytes(Na, Nb, n, 4, "fp64") == 0
+    ok = dict(Xa=v(1), Na=Na, Xb=v(5), Nb=Nb, n=n, reps=2, prec=2, K=v(2), ldk=Nb, lg=None, ldl=0, ws=v(3), wsb=need)
+    def call(**kw):
+        a = dict(ok); a.update(kw)
+        return L.qsvm_cross_host(a["Xa"], a["Na"], a["Xb"], a["Nb"], a["n"], a["reps"], a["prec"], a["K"], a["ldk"],
+                                 a["lg"], a["ldl"], a["ws"], a["wsb"], None)
+    assert call(Xa=None) == qsvm.QSVM_ERR_ARG
+    assert call(Xb=None) == qsvm.QSVM_ERR_ARG
+    assert call(K=None) == qsvm.QSVM_ERR_ARG
+    assert call(ldk=Nb - 1) == qsvm.QSVM_ERR_ARG
+    assert call(lg=v(4), ldl=Nb - 1) == qsvm.QSVM_ERR_ARG
+    assert call(lg=v(4), ldl=Nb) == qsvm.QSVM_ERR_ARG  # ws sized without logK
+    assert call(ws=None) == qsvm.QSVM_ERR_ARG
+    assert call(ws=ctypes.c_void_p(256 * 3 + 16)) == qsvm.QSVM_ERR_ARG  # misaligned
+    assert call(wsb=need - 1) == qsvm.QSVM_ERR_ARG
+    assert call(Na=0) == qsvm.QSVM_ERR_ARG
+    assert call(Nb=0) == qsvm.QSVM_ERR_ARG
+    assert call(reps=4) == qsvm.QSVM_ERR_CHI
