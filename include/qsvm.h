@@ -218,7 +218,9 @@ int32_t qsvm_cross_host(const double* X_a, int64_t n_a, const double* X_b, int64
  * qsvm_gram_tile_dim() x qsvm_gram_tile_dim() block of pairs; with
  * T = ceil(n_points / tile_dim), tiles (ti, tj), ti <= tj, are numbered in bands
  * of 8 tile rows, within a band column by column, within a column row by row
- * (the order the kernels visit them in; qsvm_gram_tile_coords decodes it).
+ * (the order the kernels visit them in; qsvm_gram_tile_coords decodes one,
+ * qsvm_gram_tile_list the range [tile_begin, tile_end) into host arrays ti, tj of
+ * tile_end - tile_begin entries each, owned by the caller).
  * qsvm_gram_partition splits [0, tiles) into `world` contiguous ranges of
  * near-equal pair count; qsvm_kernel_gram_tiles computes one range (writing both
  * K[i][j] and its mirror for every pair in it).  All but qsvm_kernel_gram_tiles
@@ -229,6 +231,8 @@ int32_t qsvm_gram_partition(int64_t n_points, int32_t reps, int32_t precision, i
                             int64_t* tile_begin, int64_t* tile_end);
 int32_t qsvm_gram_tile_coords(int64_t n_points, int32_t reps, int32_t precision, int64_t tile, int64_t* ti,
                               int64_t* tj);
+int32_t qsvm_gram_tile_list(int64_t n_points, int32_t reps, int32_t precision, int64_t tile_begin,
+                            int64_t tile_end, int64_t* ti, int64_t* tj);
 int32_t qsvm_kernel_gram_tiles(const void* mps, int64_t n_points, int32_t n_qubits, int32_t reps,
                                int32_t precision, int64_t tile_begin, int64_t tile_end, double* K, int64_t ldk,
                                double* logK, int64_t ldl, void* stream);

@@ -291,6 +291,20 @@ int32_t qsvm_gram_tile_coords(int64_t n_points, int32_t reps, int32_t precision,
   return QSVM_OK;
 }
 
+int32_t qsvm_gram_tile_list(int64_t n_points, int32_t reps, int32_t precision, int64_t tile_begin,
+                            int64_t tile_end, int64_t* ti, int64_t* tj) {
+  const int64_t total = qsvm_gram_num_tiles(n_points, reps, precision);
+  if (total <= 0) return fail(QSVM_ERR_ARG, "no tiles for n_points=%lld reps=%d precision=%d", (long long)n_points,
+                              reps, precision);
+  if (tile_begin < 0 || tile_end < tile_begin || tile_end > total)
+    return fail(QSVM_ERR_ARG, "tile range [%lld, %lld) outside [0, %lld]", (long long)tile_begin,
+                (long long)tile_end, (long long)total);
+  if (tile_end > tile_begin && (!ti || !tj)) return fail(QSVM_ERR_ARG, "null output pointer");
+  const int64_t T = tiles_per_side(n_points, qsvm_gram_tile_dim(reps, precision));
+  for (int64_t b = tile_begin; b < tile_end; ++b) sym_tile_decode(b, T, ti[b - tile_begin], tj[b - tile_begin]);
+  return QSVM_OK;
+}
+
 int32_t qsvm_kernel_gram_tiles(const void* mps, int64_t n_points, int32_t n_qubits, int32_t reps,
                                int32_t precision, int64_t tile_begin, int64_t tile_end, double* K, int64_t ldk,
                                double* logK, int64_t ldl, void* stream) {

@@ -68,6 +68,7 @@ _SIGS = {
     "qsvm_gram_num_tiles": (_i64, [_i64, _i32, _i32]),
     "qsvm_gram_partition": (_i32, [_i64, _i32, _i32, _i32, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "qsvm_gram_tile_coords": (_i32, [_i64, _i32, _i32, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "qsvm_gram_tile_list": (_i32, [_i64, _i32, _i32, _i64, _i64, _vp, _vp]),
     "qsvm_kernel_gram_tiles": (_i32, [_vp, _i64, _i32, _i32, _i32, _i64, _i64, _dp, _i64, _dp, _i64, _vp]),
     "qsvm_batch_workspace_bytes": (_sz, [_i32]),
     "qsvm_kernel_batch": (_i32, [ctypes.POINTER(QsvmJob), _i32, _i32, _i32, _vp, _sz, _vp]),
@@ -173,6 +174,17 @@ def qsvm_gram_tile_coords(n_points: int, reps: int, precision, tile: int):
     a, b = _i64(0), _i64(0)
     _check(lib().qsvm_gram_tile_coords(n_points, reps, _prec(precision), tile, ctypes.byref(a), ctypes.byref(b)))
     return int(a.value), int(b.value)
+
+
+def qsvm_gram_tile_list(n_points: int, reps: int, precision, tile_begin: int, tile_end: int):
+    """(ti, tj) int64 numpy arrays of the Gram tiles [tile_begin, tile_end) in the kernels' order."""
+    import numpy as np
+    m = tile_end - tile_begin
+    ti = np.empty(max(m, 0), dtype=np.int64)
+    tj = np.empty(max(m, 0), dtype=np.int64)
+    _check(lib().qsvm_gram_tile_list(n_points, reps, _prec(precision), tile_begin, tile_end,
+                                     ti.ctypes.data if m > 0 else None, tj.ctypes.data if m > 0 else None))
+    return ti, tj
 
 
 # ---------------------------------------------------------------- compute ---
