@@ -175,8 +175,9 @@ int32_t qsvm_kernel_cross(const void* mps_a, int64_t n_a, const void* mps_b, int
  * and its Gram computed, and K (HOST float64, ldk >= n_points) and, if logK
  * (HOST or NULL, ldl >= n_points) is given, ln K are copied back.  Page-locked
  * host memory lets the copies run asynchronously; pageable memory works but the
- * copies then synchronise with the host.  The Gram runs in about eight launches of
- * whole tile bands, alternating between `stream` and a second compute stream (they
+ * copies then synchronise with the host.  The Gram runs in up to eight launches of
+ * whole tile bands (one for small problems: each launch gets at least four tiles
+ * per SM), alternating between `stream` and a second compute stream (they
  * write disjoint tiles); once launches 0..c have completed, the rows of launch c
  * are final (a band's rows receive mirror writes only from earlier bands) and a
  * copy stream takes them to the host while later launches compute.
@@ -199,8 +200,10 @@ int32_t qsvm_gram_host(const double* X, int64_t n_points, int32_t n_qubits, int3
  * n_a x n_qubits float64, the test points) and X_b (HOST, n_b x n_qubits, the train
  * points) are copied to the device and their MPS built; the kernel (K[i*ldk + j] as in
  * qsvm_kernel_cross, HOST float64, ldk >= n_b; logK HOST or NULL, ldl >= n_b) runs in
- * about eight launches of whole tile rows, and each launch's rows are copied to the
- * host on a second stream while the next launch computes.
+ * up to eight launches of whole tile rows (one for small problems: each launch gets at
+ * least four tiles per SM), alternating between `stream` and a second compute stream,
+ * and each launch's rows are copied to the host on a third stream while later
+ * launches compute.
  *   ws  device scratch of qsvm_cross_host_workspace_bytes(n_a, n_b, n_qubits, reps,
  *       precision, logK != NULL) bytes, 256-byte aligned, owned by the caller.
  * Stream-ordered on `stream` as qsvm_gram_host (the same capture and workspace

@@ -354,6 +354,19 @@ int32_t qsvm_kernel_cross(const void* mps_a, int64_t n_a, const void* mps_b, int
 // Device scratch of qsvm_gram_host: X, the MPS, K (and logK), each 256-byte aligned.
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Number of chunks a host-buffer call splits its launches into: at most kMaxChunks,
+// and at least 4 CTAs (one per tile) per SM in each, so small problems run as one
+// launch instead of several that each leave most SMs idle.
+constexpr int kMaxChunks = 8;
+static int host_chunks(int64_t tiles) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                               cudaSuccess || sms < 1)
+    sms = 1;
+  const int64_t c = tiles / (4 * (int64_t)sms);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kMaxChunks, c));
+}
+
 size_t qsvm_gram_host_workspace_bytes(int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
                                       int32_t with_logk) {
   if (n_points < 1 || n_qubits < 2) return 0;
@@ -390,18 +403,19 @@ int32_t qsvm_gram_host(const double* X, int64_t n_points, int32_t n_qubits, int3
   rc = qsvm_build_mps(dX, N, n_qubits, reps, precision, dM, mps_bytes, stream);
   if (rc) return rc;
 
-  // Chunks of whole tile bands, about kChunks of them by tile count.  Bands run in
+  // Chunks of whole tile bands, up to kMaxChunks of them by tile count.  Bands run in
   // order and a band's rows receive mirror writes only from earlier bands, so the
   // rows of chunk c are final once chunks 0..c have completed: a copy stream, which
   // waits for each chunk in turn, copies them out while later chunks compute.  The
   // chunks write disjoint tiles, so consecutive chunks alternate between the caller's
   // stream and a second compute stream: a launch fills the SMs its predecessor's last
   // wave leaves idle.
-  constexpr int kChunks = 8;
+  constexpr int kChunks = kMaxChunks;
   const int tdim = pair_tile_dim(1 << reps, precision);
   const int64_t T = tiles_per_side(N, tdim);
   const int64_t total = T * (T + 1) / 2;
   const int64_t nbands = (T + kBandRows - 1) / kBandRows;
+  const int nch = host_chunks(total);
   auto band_start = [&](int64_t b) { return b >= nbands ? total : sym_band_start(b, T); };
   cudaStream_t cs = nullptr, xs = nullptr;  // second compute stream, copy stream
   cudaEvent_t ev[kChunks + 3] = {};         // chunks, build, joins of cs and xs
@@ -413,8 +427,8 @@ int32_t qsvm_gram_host(const double* X, int64_t n_points, int32_t n_qubits, int3
   int64_t b0 = 0;
   for (int c = 0; e == cudaSuccess && rc == QSVM_OK && b0 < nbands; ++c) {
     int64_t b1 = b0 + 1;  // the last chunk takes every remaining band
-    while (c < kChunks - 1 && b1 < nbands && band_start(b1) * kChunks < total * (int64_t)(c + 1)) ++b1;
-    if (c == kChunks - 1) b1 = nbands;
+    while (c < nch - 1 && b1 < nbands && band_start(b1) * nch < total * (int64_t)(c + 1)) ++b1;
+    if (c == nch - 1) b1 = nbands;
     cudaStream_t run = (c & 1) ? cs : st;
     rc = gram_launch(dM, N, n_qubits, reps, precision, band_start(b0), band_start(b1), dK, N, dL, N, run);
     if (rc) break;
@@ -491,24 +505,31 @@ int32_t qsvm_cross_host(const double* X_a, int64_t n_a, const double* X_b, int64
   if (!rc) rc = qsvm_build_mps(dXb, n_b, n_qubits, reps, precision, dMb, mb, stream);
   if (rc) return rc;
 
-  // Row chunks of whole tile rows: the rows of a chunk are final when its launch
-  // completes, and a copy stream takes them to the host while the next one computes.
-  constexpr int kChunks = 8;
+  // Row chunks of whole tile rows, up to kMaxChunks of them: the rows of a chunk are
+  // final when its launch completes, and a copy stream takes them to the host while
+  // later chunks compute.  Chunks write disjoint rows, so they alternate between the
+  // caller's stream and a second compute stream, as in qsvm_gram_host.
+  constexpr int kChunks = kMaxChunks;
   const int tdim = pair_tile_dim(1 << reps, precision);
-  const int64_t Ta = tiles_per_side(n_a, tdim);
-  const int64_t rows_per_chunk = ((Ta + kChunks - 1) / kChunks) * tdim;
+  const int64_t Ta = tiles_per_side(n_a, tdim), Tb = tiles_per_side(n_b, tdim);
+  const int nch = host_chunks(Ta * Tb);
+  const int64_t rows_per_chunk = ((Ta + nch - 1) / nch) * tdim;
   const size_t point_bytes = qsvm_mps_point_bytes(n_qubits, reps, precision);
-  cudaStream_t xs = nullptr;
-  cudaEvent_t ev[kChunks + 1] = {};
-  e = cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking);
-  for (int c = 0; e == cudaSuccess && c <= kChunks; ++c) e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming);
-  for (int c = 0; e == cudaSuccess && rc == QSVM_OK && c < kChunks; ++c) {
+  cudaStream_t cs = nullptr, xs = nullptr;  // second compute stream, copy stream
+  cudaEvent_t ev[kChunks + 3] = {};         // chunks, build, joins of cs and xs
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking);
+  for (int c = 0; e == cudaSuccess && c < kChunks + 3; ++c) e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[kChunks], st);  // both MPS are built
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[kChunks], 0);
+  for (int c = 0; e == cudaSuccess && rc == QSVM_OK && c < nch; ++c) {
     const int64_t r0 = c * rows_per_chunk, r1 = std::min<int64_t>(n_a, r0 + rows_per_chunk);
     if (r0 >= r1) break;
+    cudaStream_t run = (c & 1) ? cs : st;
     rc = qsvm_kernel_cross(dMa + (size_t)r0 * point_bytes, r1 - r0, dMb, n_b, n_qubits, reps, precision,
-                           dK + r0 * n_b, n_b, dL ? dL + r0 * n_b : nullptr, n_b, stream);
+                           dK + r0 * n_b, n_b, dL ? dL + r0 * n_b : nullptr, n_b, run);
     if (rc) break;
-    e = cudaEventRecord(ev[c], st);
+    e = cudaEventRecord(ev[c], run);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, ev[c], 0);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(K + r0 * ldk, (size_t)ldk * sizeof(double), dK + r0 * n_b, (size_t)n_b * sizeof(double),
@@ -517,14 +538,23 @@ int32_t qsvm_cross_host(const double* X_a, int64_t n_a, const double* X_b, int64
       e = cudaMemcpy2DAsync(logK + r0 * ldl, (size_t)ldl * sizeof(double), dL + r0 * n_b, (size_t)n_b * sizeof(double),
                             (size_t)n_b * sizeof(double), (size_t)(r1 - r0), cudaMemcpyDeviceToHost, xs);
   }
-  cudaError_t e2 = (xs && ev[kChunks]) ? cudaEventRecord(ev[kChunks], xs) : cudaSuccess;
-  if (xs && ev[kChunks] && e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, ev[kChunks], 0);
+  // join both helper streams back into the caller's stream (also after an error), then
+  // release them (deferred)
+  cudaError_t e2 = cudaSuccess;
+  cudaStream_t helpers[2] = {cs, xs};
+  for (int h = 0; h < 2; ++h) {
+    if (!helpers[h] || !ev[kChunks + 1 + h]) continue;
+    cudaError_t r = cudaEventRecord(ev[kChunks + 1 + h], helpers[h]);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(st, ev[kChunks + 1 + h], 0);
+    if (r != cudaSuccess && e2 == cudaSuccess) e2 = r;
+  }
   for (auto& x : ev)
     if (x) cudaEventDestroy(x);
-  if (xs) cudaStreamDestroy(xs);
+  for (auto h : helpers)
+    if (h) cudaStreamDestroy(h);
   if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(e, "chunked copy of the cross kernel to the host");
-  if (e2 != cudaSuccess) return cuda_fail(e2, "joining the copy stream");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "joining the helper streams");
   return QSVM_OK;
 }
 

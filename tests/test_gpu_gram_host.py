@@ -1,6 +1,6 @@
 """qsvm_gram_host (host X in, host K out, the Gram in chunks of tile bands with the
 row bands of K copied out while later chunks compute) against the device path:
-bit-identical results for one chunk, several chunks and the full eight, with a
+bit-identical results for one chunk (small problems) and up to eight, with a
 strided host K and with logK; qsvm_cross_host (the test x train kernel of host data, in
 row chunks copied out as they finish) against qsvm_build_mps + qsvm_kernel_cross."""
 import numpy as np
@@ -48,7 +48,7 @@ def test_gram_host_pageable_and_default_buffers(q):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_split", "fp32"])
 @pytest.mark.parametrize("Na,Nb,n,reps", [(1, 1, 2, 2), (37, 5, 13, 1), (300, 170, 24, 2), (1000, 40, 6, 2),
-                                          (129, 200, 9, 3)])
+                                          (129, 200, 9, 3), (2500, 1000, 4, 2)])
 def test_cross_host_matches_device(q, prec, Na, Nb, n, reps):
     Xa = inputs.uniform_features(Na, n, 1900 + Na)
     Xb = inputs.uniform_features(Nb, n, 2900 + Nb)
