@@ -1,6 +1,7 @@
 """The C ABI driven from a plain C program on the GPU: cudaMalloc'd buffers, MPS build
 and Grams in split FP32 and FP64 through include/qsvm.h, checked for K_ii = 1, exact
-symmetry and split-vs-FP64 agreement.  No Python or PyTorch on the data path."""
+symmetry and split-vs-FP64 agreement; then the host-buffer calls qsvm_gram_host
+(bit-identical to the device Gram) and qsvm_cross_host (against the FP64 Gram's rows).  No Python or PyTorch on the data path."""
 import os
 import shutil
 import subprocess
@@ -53,9 +54,26 @@ int main(void) {
       if (a < kmin) kmin = a;
       if (a > kmax) kmax = a;
     }
+  /* host in, host out: the Gram (bit-identical to the device path) and 10 test points x N */
+  const int Nt = 10;
+  size_t wg = qsvm_gram_host_workspace_bytes(N, n, reps, QSVM_FP32_SPLIT, 0);
+  size_t wx = qsvm_cross_host_workspace_bytes(Nt, N, n, reps, QSVM_FP32_SPLIT, 0);
+  void *wsg = NULL, *wsx = NULL;
+  double *K3 = (double*)malloc(sizeof(double) * N * N), *Kx = (double*)malloc(sizeof(double) * Nt * N);
+  if (cudaMalloc(&wsg, wg) != cudaSuccess || cudaMalloc(&wsx, wx) != cudaSuccess) return 1;
+  CK(qsvm_gram_host(X, N, n, reps, QSVM_FP32_SPLIT, K3, N, NULL, 0, wsg, wg, NULL));
+  CK(qsvm_cross_host(X, Nt, X, N, n, reps, QSVM_FP32_SPLIT, Kx, N, NULL, 0, wsx, wx, NULL));
+  if (cudaDeviceSynchronize() != cudaSuccess) return 1;
+  double hostdiff = 0, crossdiff = 0;
+  for (int i = 0; i < N * N; ++i)
+    if (K3[i] != K1[i]) hostdiff = 1;
+  for (int i = 0; i < Nt; ++i)
+    for (int j = 0; j < N; ++j)
+      if (fabs(Kx[i * N + j] - K2[i * N + j]) > crossdiff) crossdiff = fabs(Kx[i * N + j] - K2[i * N + j]);
   int32_t status = -1;
   CK(qsvm_device_status(NULL, 0, &status));
-  printf("diag %.3e asym %g dk %.3e kmin %.3e kmax %.6f status %d\n", diag, asym, dk, kmin, kmax, (int)status);
+  printf("diag %.3e asym %g dk %.3e kmin %.3e kmax %.6f hostdiff %g crossdk %.3e status %d\n", diag, asym, dk, kmin,
+         kmax, hostdiff, crossdiff, (int)status);
   return 0;
 }
 """
@@ -83,4 +101,5 @@ def test_c_program_end_to_end(tmp_path):
     vals = dict(zip(v[0::2], v[1::2]))
     assert float(vals["diag"]) <= 1e-6 and float(vals["asym"]) == 0.0
     assert float(vals["dk"]) <= 1e-6 and 0.0 <= float(vals["kmin"]) and float(vals["kmax"]) <= 1.0 + 1e-6
+    assert float(vals["hostdiff"]) == 0.0 and float(vals["crossdk"]) <= 1e-6
     assert int(vals["status"]) == 0
