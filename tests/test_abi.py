@@ -265,3 +265,28 @@ def test_cross_host_arguments():
     assert call(Na=0) == qsvm.QSVM_ERR_ARG
     assert call(Nb=0) == qsvm.QSVM_ERR_ARG
     assert call(reps=4) == qsvm.QSVM_ERR_CHI
+
+
+def test_gram_tile_list():
+    """qsvm_gram_tile_list decodes a tile range into host arrays (the kernels' order:
+    equal to qsvm_gram_tile_coords tile by tile), an empty range needs no arrays, and a
+    range outside [0, tiles] is an argument error."""
+    import ctypes
+    N, reps, prec = 300, 2, "fp32_split"
+    total = qsvm.qsvm_gram_num_tiles(N, reps, prec)
+    ti, tj = qsvm.qsvm_gram_tile_list(N, reps, prec, 5, total - 3)
+    assert len(ti) == total - 8
+    assert list(zip(ti, tj)) == [qsvm.qsvm_gram_tile_coords(N, reps, prec, b) for b in range(5, total - 3)]
+    assert len(qsvm.qsvm_gram_tile_list(N, reps, prec, 7, 7)[0]) == 0
+    L = qsvm.lib()
+    buf = (ctypes.c_int64 * 4)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.qsvm_gram_tile_list(N, reps, 2, -1, 2, p, p) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_gram_tile_list(N, reps, 2, 3, 2, p, p) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_gram_tile_list(N, reps, 2, total - 1, total + 1, p, p) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_gram_tile_list(N, reps, 2, 0, 2, None, None) == qsvm.QSVM_ERR_ARG
+    assert L.qsvm_gram_tile_list(0, reps, 2, 0, 0, None, None) == qsvm.QSVM_ERR_ARG
+    # the union of every rank's range covers each tile once, in order
+    from paper_2405_02630_gb300 import shard
+    allt = [t for r in range(5) for t in zip(*shard.rank_tiles(N, reps, prec, 5, r))]
+    assert allt == list(zip(*qsvm.qsvm_gram_tile_list(N, reps, prec, 0, total)))
