@@ -333,3 +333,56 @@ def test_full_size_gram_sampled(q, oracle):
     assert np.max(np.abs(Kg - Ko)) <= 1e-6
     m = Ko > 1e-300
     assert np.max(np.abs(LKg[m] - LKo[m])) <= 1e-5
+
+
+def _sampled_pairs(N, seed, n_diag=256, n_rand=256, Nb=None):
+    rng = np.random.default_rng(seed)
+    di = rng.choice(N, min(n_diag, N), replace=False)
+    ia = np.concatenate([di, rng.integers(0, N, n_rand)])
+    ib = np.concatenate([di if Nb is None else rng.integers(0, Nb, di.size), rng.integers(0, Nb or N, n_rand)])
+    return ia, ib
+
+
+def test_full_size_gram_fp64_sampled(q, oracle):
+    """The FP64 path at n = 784, reps = 2, N = 8192: bit-exact symmetry and |dK| <= 1e-10
+    against the oracle on sampled entries (diagonal included)."""
+    X, _, n, reps = inputs.workload("gram_n784_r2_N8192")
+    K, LK = q.gram(_dev(X), reps, "fp64", logK=True)
+    torch.cuda.synchronize()
+    assert q.qsvm_device_status() == 0
+    assert torch.equal(K, K.T)
+    ia, ib = _sampled_pairs(X.shape[0], 1)
+    Ko, LKo = oracle.mps_pairs(X, X, ia, ib, reps)
+    Kg = K[torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda()].cpu().numpy()
+    LKg = LK[torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda()].cpu().numpy()
+    _check(Kg, Ko, "fp64", "full-size FP64 gram, sampled", LKg, LKo)  # |dK| <= 1e-10
+
+
+def test_full_size_gram_reps3_sampled(q, oracle):
+    """n = 784, reps = 3, N = 8192 (the four-thread engine, 8 x 8 tiles), split FP32:
+    bit-exact symmetry and sampled entries against the oracle."""
+    X, _, n, reps = inputs.workload("cfg4_n784_r3_N8192")
+    K, LK = q.gram(_dev(X), reps, "fp32_split", logK=True)
+    torch.cuda.synchronize()
+    assert q.qsvm_device_status() == 0
+    assert torch.equal(K, K.T)
+    ia, ib = _sampled_pairs(X.shape[0], 2, 128, 128)
+    Ko, LKo = oracle.mps_pairs(X, X, ia, ib, reps)
+    Kg = K[torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda()].cpu().numpy()
+    LKg = LK[torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda()].cpu().numpy()
+    _check(Kg, Ko, "fp32_split", "full-size reps 3 gram, sampled", LKg, LKo)
+
+
+@pytest.mark.parametrize("prec", ["fp32_split", "fp64"])
+def test_full_size_cross_sampled(q, oracle, prec):
+    """The 1024 x 2048 test x train kernel of the n = 784 MNIST-like workload (the launch
+    the bench times) on sampled entries against the oracle."""
+    Xtr, Xte, n, reps = inputs.workload("cfg2_n784_r2_N2048x1024")
+    K, LK = q.cross(_dev(Xte), _dev(Xtr), reps, prec, logK=True)
+    torch.cuda.synchronize()
+    assert q.qsvm_device_status() == 0
+    ia, ib = _sampled_pairs(Xte.shape[0], 3, 0, 512, Nb=Xtr.shape[0])
+    Ko, LKo = oracle.mps_pairs(Xte, Xtr, ia, ib, reps)
+    Kg = K[torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda()].cpu().numpy()
+    LKg = LK[torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda()].cpu().numpy()
+    _check(Kg, Ko, prec, "full-size cross, sampled", LKg, LKo)
