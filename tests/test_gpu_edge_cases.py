@@ -1,5 +1,5 @@
-"""Edge cases of the CUDA path: very long chains, degenerate inputs and ragged
-shapes, against the oracle or exact values."""
+"""Edge cases of the CUDA path: very long chains, degenerate inputs, ragged shapes and
+offsets past 32 bits, against the oracle or exact values."""
 import numpy as np
 import pytest
 
@@ -85,3 +85,51 @@ def test_wide_angle_range(q, oracle, prec, reps):
     K, _ = q.gram(torch.from_numpy(X).cuda(), reps, prec)
     Ko, _ = oracle.mps_gram(X, reps)
     assert np.max(np.abs(K.cpu().numpy() - Ko)) <= TOL[prec]
+
+
+def test_gram_offsets_beyond_32_bits(q, oracle):
+    """A 66 000-point Gram (n = 3, split FP32, a ragged last tile): K holds 4.36e9 entries,
+    so its element offsets pass 2^32.  Sampled entries, many in the last rows, against the
+    oracle, and their mirrors bit-exact."""
+    N, n, reps = 66000, 3, 2
+    X = inputs.uniform_features(N, n, 123)
+    K, _ = q.gram(torch.from_numpy(X).cuda(), reps, "fp32_split")
+    torch.cuda.synchronize()
+    assert q.qsvm_device_status() == 0
+    rng = np.random.default_rng(5)
+    ia = np.concatenate([rng.integers(0, N, 128), rng.integers(65100, N, 128), np.arange(N - 16, N)])
+    ib = np.concatenate([rng.integers(0, N, 128), rng.integers(0, N, 128), np.arange(N - 16, N)])
+    assert (ia.astype(np.int64) * N + ib).max() >= 2 ** 32
+    ta, tb = torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda()
+    Kg, Kt = K[ta, tb].cpu().numpy(), K[tb, ta].cpu().numpy()
+    del K
+    torch.cuda.empty_cache()
+    Ko, _ = oracle.mps_pairs(X, X, ia, ib, reps)
+    assert np.max(np.abs(Kg - Ko)) <= TOL["fp32_split"]
+    assert np.array_equal(Kg, Kt)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split"])
+def test_cross_record_offsets_beyond_31_bits(q, oracle, prec):
+    """8 test points against 70 000 train points at n = 784: the train records span 3.5 GB
+    (FP64) or 7 GB (split, two arrays), so record offsets pass 2^31; sampled entries, many
+    against the last train points, against the oracle."""
+    Ntr, n, reps = 70000, 784, 2
+    Xtr = inputs.mnist_like_features(Ntr, n, 124)
+    Xte = inputs.mnist_like_features(8, n, 125)
+    Xte[3] = Xtr[Ntr - 1]  # K = 1 against the last train point
+    K, LK = q.cross(torch.from_numpy(Xte).cuda(), torch.from_numpy(Xtr).cuda(), reps, prec, logK=True)
+    torch.cuda.synchronize()
+    assert q.qsvm_device_status() == 0
+    rng = np.random.default_rng(6)
+    ia = np.concatenate([rng.integers(0, 8, 96), rng.integers(0, 8, 96), [3]])
+    ib = np.concatenate([rng.integers(0, Ntr, 96), rng.integers(60000, Ntr, 96), [Ntr - 1]])
+    ta, tb = torch.from_numpy(ia).cuda(), torch.from_numpy(ib).cuda()
+    Kg, Lg = K[ta, tb].cpu().numpy(), LK[ta, tb].cpu().numpy()
+    del K, LK
+    torch.cuda.empty_cache()
+    Ko, LKo = oracle.mps_pairs(Xte, Xtr, ia, ib, reps)
+    assert np.max(np.abs(Kg - Ko)) <= TOL[prec]
+    assert abs(Kg[-1] - 1.0) <= TOL[prec]
+    m = Ko > 1e-300
+    assert np.max(np.abs(Lg[m] - LKo[m])) <= (1e-8 if prec == "fp64" else 1e-5)
