@@ -79,7 +79,7 @@ def _run(tmp_path, world, N, n, reps):
                        start_method="spawn")
 
 
-@pytest.mark.parametrize("world,N", [(2, 45), (3, 45), (3, 20)])
+@pytest.mark.parametrize("world,N", [(2, 45), (3, 45), (3, 20), (4, 61)])
 def test_sharded_gram_matches_single_rank(tmp_path, oracle, world, N):
     """N = 20 at reps = 2 is two tile rows, three tiles: with three ranks one rank may own
     none, and the gather still assembles the Gram."""
