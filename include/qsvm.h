@@ -223,7 +223,8 @@ int32_t qsvm_cross_host(const double* X_a, int64_t n_a, const double* X_b, int64
  * of 8 tile rows, within a band column by column, within a column row by row
  * (the order the kernels visit them in; qsvm_gram_tile_coords decodes one,
  * qsvm_gram_tile_list the range [tile_begin, tile_end) into host arrays ti, tj of
- * tile_end - tile_begin entries each, owned by the caller).
+ * tile_end - tile_begin entries each, owned by the caller; QSVM_ERR_ARG for a range
+ * outside [0, tiles], no tiles at all, or null arrays with a non-empty range).
  * qsvm_gram_partition splits [0, tiles) into `world` contiguous ranges of
  * near-equal pair count; qsvm_kernel_gram_tiles computes one range (writing both
  * K[i][j] and its mirror for every pair in it).  All but qsvm_kernel_gram_tiles
