@@ -80,10 +80,30 @@ FMA_PER_CMAC = {"fp32": 4, "fp32_split": 12, "fp64": 4}
 
 # DRAM bytes (read + write) of one pair-kernel launch, from one ncu capture of the
 # same configuration with the default pipeline shape (dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass over the full-size launch).  Configurations not
-# captured with the current kernel report null.
-MEASURED_TRAFFIC_BYTES = {("gram_n784_r2_N8192", "fp32_split"): 13_559_001_600 + 549_287_424,
-                          ("cfg4_n784_r3_N8192", "fp32_split"): 26_363_485_696 + 583_596_544}
+# dram__bytes_write.sum, one pass over the full-size launch), each stored with the
+# digest of the kernel sources it was captured on (kernel_digest()).  A configuration
+# not captured, or captured on other kernel sources, reports null.
+MEASURED_TRAFFIC_BYTES = {
+    ("gram_n784_r2_N8192", "fp32_split"): ("f539097c8c72144e", 13_559_001_600 + 549_287_424),
+}
+KERNEL_SOURCES = ("pair_contract.cuh", "pair_contract.cu", "qsvm_common.cuh")
+
+
+def kernel_digest() -> str:
+    """sha256 (first 16 hex digits) of the pair-kernel sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2405_02630_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, prec: str):
+    entry = MEASURED_TRAFFIC_BYTES.get((workload, prec))
+    if entry is None or entry[0] != kernel_digest():
+        return None
+    return entry[1]
 
 
 class ClockSampler:
@@ -321,17 +341,20 @@ def run_ours(args):
     if cfg >= 0:
         pipeline["sites_per_chunk"], pipeline["stages"] = qsvm.qsvm_config_info(cfg, reps, P)
 
-    def step(prec_code=P, tile_range=(tb, te)):
+    LK = LKx = None  # ln K outputs, allocated for the timing with ln K written
+
+    def step(prec_code=P, tile_range=(tb, te), with_logk=False):
         qsvm.qsvm_build_mps(Xd, reps, prec_code, mps=mps, stream=stream)
         if Nte:
             qsvm.qsvm_build_mps(Xted, reps, prec_code, mps=mps_te, stream=stream)
         ev_mid = torch.cuda.Event(enable_timing=True)
         ev_mid.record(stream)
-        qsvm.qsvm_kernel_gram_tiles(mps, N, n, reps, prec_code, tile_range[0], tile_range[1], K, stream=stream)
+        qsvm.qsvm_kernel_gram_tiles(mps, N, n, reps, prec_code, tile_range[0], tile_range[1], K,
+                                    logK=LK if with_logk else None, stream=stream)
         if Nte and a1 > a0:
             stride = qsvm.qsvm_mps_point_bytes(n, reps, prec_code)
             qsvm.qsvm_kernel_cross(mps_te[a0 * stride:], a1 - a0, mps, N, n, reps, prec_code, K=Kx[a0:a1],
-                                   stream=stream)
+                                   logK=LKx[a0:a1] if with_logk else None, stream=stream)
         return ev_mid
 
     def barrier():
@@ -364,12 +387,33 @@ def run_ours(args):
     if status != 0:
         raise RuntimeError(f"device status {status}")
 
+    # the same step with ln K written beside K (the default output of the Python API):
+    # reported beside the K-only headline, same timing rules, up to three steps
+    LK = torch.empty((N, N), dtype=torch.float64, device=dev)
+    LKx = torch.empty((Nte, N), dtype=torch.float64, device=dev) if Nte else None
+    step(with_logk=True)
+    barrier()
+    log_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(with_logk=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        log_ms.append(e0.elapsed_time(e1))
+    del LK, LKx
+    LK = LKx = None
+
     ms = sum(step_ms) / len(step_ms)
     kms = sum(kern_ms) / len(kern_ms)
+    lms = sum(log_ms) / len(log_ms)
     if world > 1:
-        t = torch.tensor([ms, kms], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms, kms, lms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, kms = float(t[0]), float(t[1])
+        ms, kms, lms = float(t[0]), float(t[1]), float(t[2])
     value = total_pairs / (ms * 1e-3)
 
     # ---- roofline of the dominant kernel (the pair contraction) ----
@@ -385,8 +429,9 @@ def run_ours(args):
         bound = "alu"
     fma_frac = (FMA_PER_CMAC[prec] * 2.0 * cm * pairs_rank / (kms * 1e-3) / 1e12) / peak
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": MEASURED_TRAFFIC_BYTES.get((args.workload, prec)) if world == 1 else None,
+                "traffic": measured_traffic(args.workload, prec) if world == 1 else None,
                 "traffic_unit": "bytes per launch (ncu)",
+                "kernel_digest": kernel_digest(),
                 "kernel": f"pair_tile_kernel<chi={2 ** reps},{prec}>",
                 "peak_basis": (f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x 2 x {mhz:.0f} MHz"
                                if prec != "fp64" else "nominal FP64 1.25 TFLOP/s"),
@@ -415,6 +460,8 @@ def run_ours(args):
         "clocks": clocks,
         "pair_kernel_ms": kms,
         "qubit_pair_sites_per_s": value * n,
+        "with_logK": {"ms_per_step": lms, "entries_per_s": total_pairs / (lms * 1e-3), "steps": len(log_ms),
+                      "note": "same step with ln K written beside K (the API default); value is K only"},
     }
 
     if rank == 0 and world == 1 and not args.quick:
@@ -449,23 +496,34 @@ def run_ours(args):
             Kxg = Kx[torch.from_numpy(xa).to(dev), torch.from_numpy(xb).to(dev)].cpu().numpy()
             acc["cross_pairs"] = int(ns)
             acc["cross_max_abs_dK"] = float(np.max(np.abs(Kxg - Kxo)))
-        # near-duplicate pairs, K spread over (0, 1): where |dK| is informative
-        base = inputs.mnist_like_features(24, n, 21) if n >= 64 else inputs.uniform_features(24, n, 21)
-        pert = inputs.near_duplicates(base, 22)
-        Knd_o, LKnd_o = oracle.mps_cross(base, pert, reps)
-        Knd, LKnd = qsvm.cross(torch.from_numpy(base).to(dev), torch.from_numpy(pert).to(dev), reps, prec, logK=True)
-        d = np.abs(Knd.cpu().numpy() - Knd_o)
-        big = Knd_o > 1e-300  # log10 K compared where the oracle's K is a normal double
-        dlog10 = np.abs(LKnd.cpu().numpy() - LKnd_o)[big] / np.log(10.0)
-        acc["near_dup"] = {"pairs": int(d.size), "K_range": [float(Knd_o.min()), float(Knd_o.max())],
+        # near-duplicate pairs, K spread over (0, 1): where |dK| is informative.  A Gram
+        # of 24 base rows with three perturbed copies each, shuffled, through the same
+        # symmetric Gram kernel as the timed step: such pairs fall in diagonal tiles
+        # (masked half tile, mirror) and in off-diagonal tiles.  Every entry i < j.
+        Xnd, _ = inputs.near_duplicate_clusters(24, 4, n, 40)
+        Knd_o, LKnd_o = oracle.mps_gram(Xnd, reps)
+        Knd, LKnd = qsvm.gram(torch.from_numpy(Xnd).to(dev), reps, prec, logK=True)
+        Knd, LKnd = Knd.cpu().numpy(), LKnd.cpu().numpy()
+        iu, ju = np.triu_indices(Xnd.shape[0], 1)
+        d = np.abs(Knd[iu, ju] - Knd_o[iu, ju])
+        inf = Knd_o[iu, ju] > 0.1
+        td_nd = qsvm.qsvm_gram_tile_dim(reps, P)
+        big = Knd_o[iu, ju] > 1e-300  # ln K compared where the oracle's K is a normal double
+        dlog10 = np.abs(LKnd[iu, ju] - LKnd_o[iu, ju])[big] / np.log(10.0)
+        acc["near_dup"] = {"kernel": "qsvm_kernel_gram (symmetric Gram)", "points": int(Xnd.shape[0]),
+                           "pairs": int(d.size), "K_range": [float(Knd_o[iu, ju].min()), float(Knd_o[iu, ju].max())],
+                           "pairs_K_above_0.1": int(inf.sum()),
+                           "of_which_in_diagonal_tiles": int((inf & (iu // td_nd == ju // td_nd)).sum()),
                            "max_abs_dK": float(d.max()), "mean_abs_dK": float(d.mean()),
+                           "max_abs_dK_K_above_0.1": float(d[inf].max()),
                            "max_abs_dlog10K": float(dlog10.max()) if dlog10.size else None,
                            "log_pairs": int(dlog10.size)}
         line["accuracy_vs_oracle"] = acc
-        # the FP64 path on the same GPU, on the first tiles of the same Gram (speedup report)
+        # the FP64 path on the same GPU over the whole Gram (speedup report); with
+        # --sampled-fp64 only on its first 1/64 of the tiles
         if prec != "fp64":
             nt64 = qsvm.qsvm_gram_num_tiles(N, reps, 0)
-            nt = nt64 if args.full_fp64 else max(1, nt64 // 64)
+            nt = max(1, nt64 // 64) if args.sampled_fp64 else nt64
             mps64 = torch.empty(qsvm.qsvm_mps_bytes(n, reps, N, 0), dtype=torch.uint8, device=dev)
             qsvm.qsvm_build_mps(Xd, reps, "fp64", mps=mps64)
             K64 = torch.full((N, N), float("nan"), dtype=torch.float64, device=dev)
@@ -480,12 +538,12 @@ def run_ours(args):
             fp64_rate = sub_pairs / (e0.elapsed_time(e1) * 1e-3)
             m = ~torch.isnan(K64)
             dk = (K[m] - K64[m]).abs()
-            line["fp64_same_gpu"] = {"entries_per_s": fp64_rate, "tiles_timed": nt,
+            line["fp64_same_gpu"] = {"entries_per_s": fp64_rate, "tiles_timed": nt, "tiles_total": nt64,
                                      "speedup_of_" + prec: value / fp64_rate,
                                      "pair_kernel_speedup": (pairs_rank / (kms * 1e-3)) / fp64_rate,
                                      "entries_compared": int(m.sum()),
                                      "max_abs_dK_vs_fp64": float(dk.max()), "mean_abs_dK_vs_fp64": float(dk.mean())}
-            if Nte and args.full_fp64:
+            if Nte and not args.sampled_fp64:
                 mte64 = qsvm.qsvm_build_mps(torch.from_numpy(Xte).to(dev), reps, "fp64")
                 Kx64, _ = qsvm.qsvm_kernel_cross(mte64, Nte, mps64, N, n, reps, "fp64")
                 dx = (Kx - Kx64).abs()
@@ -519,9 +577,9 @@ def run_ours(args):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if world == 1:
-                qsvm.gram_host(Xh, reps, P, K=Kh, ws=ws_h, stream=stream)
+                qsvm.gram_host(Xh, reps, P, K=Kh, logK=False, ws=ws_h, stream=stream)
                 if Nte:
-                    qsvm.cross_host(Xteh, Xh, reps, P, K=Kxh, ws=ws_x, stream=stream)
+                    qsvm.cross_host(Xteh, Xh, reps, P, K=Kxh, logK=False, ws=ws_x, stream=stream)
             else:
                 Xd.copy_(Xh, non_blocking=True)
                 if Nte:
@@ -683,7 +741,8 @@ def main():
     ap.add_argument("--ref-pairs", type=int, default=16384)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the accuracy, FP64 and CPU side measurements")
-    ap.add_argument("--full-fp64", action="store_true", help="compare every entry with the FP64 path (small N)")
+    ap.add_argument("--sampled-fp64", action="store_true",
+                    help="time the FP64 comparison path on the first 1/64 of the Gram's tiles only")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the pipeline shape with the autotuner (on up to 4096 points) before timing")
     args = ap.parse_args()

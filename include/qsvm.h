@@ -280,10 +280,9 @@ int32_t qsvm_batch_plan_launch(qsvm_batch_plan* plan, void* stream);
 int32_t qsvm_batch_plan_destroy(qsvm_batch_plan* plan);
 
 /* qsvm_kernel_batch_noalloc -- qsvm_kernel_batch without a workspace argument,
- * for callers that cannot allocate device memory (for example code recorded
- * into a CUDA graph, where cudaMalloc is not allowed; latency-bound serving
- * loops that must avoid cudaMalloc's device-wide synchronisation; or hosts
- * whose framework allocator already owns all device memory).  The paper has no
+ * for callers that cannot allocate device memory (for example latency-bound
+ * serving loops that must avoid cudaMalloc's device-wide synchronisation, or
+ * hosts whose framework allocator already owns all device memory).  The paper has no
  * counterpart: this is an interface for such callers.  The job table and the
  * work-queue head live in a fixed 76 KiB array inside the library's device
  * image, present on every GPU that loads the library until the process exits;

@@ -131,10 +131,14 @@ int32_t gram_launch(const void* mps, int64_t n_points, int32_t n_qubits, int32_t
 
 // ---- batch job table -------------------------------------------------------
 constexpr size_t kWsAlign = 256;
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-size_t ws_jobs_offset() { return kWsAlign; }
-size_t ws_prefix_offset(int n_jobs) { return align_up(ws_jobs_offset() + sizeof(DevJob) * (size_t)n_jobs, kWsAlign); }
-size_t ws_total(int n_jobs) { return align_up(ws_prefix_offset(n_jobs) + sizeof(int64_t) * (size_t)(n_jobs + 1), kWsAlign); }
+constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr size_t ws_jobs_offset() { return kWsAlign; }
+constexpr size_t ws_prefix_offset(int n_jobs) {
+  return align_up(ws_jobs_offset() + sizeof(DevJob) * (size_t)n_jobs, kWsAlign);
+}
+constexpr size_t ws_total(int n_jobs) {
+  return align_up(ws_prefix_offset(n_jobs) + sizeof(int64_t) * (size_t)(n_jobs + 1), kWsAlign);
+}
 
 // Host image of the workspace (counter slot, sorted job table, tile prefix).
 struct BatchImage {
@@ -820,10 +824,10 @@ const char* qsvm_version(void) { return "qsvm-gb300 0.1 (sm_103a)"; }
 }  // extern "C"
 
 // ---- batch launch for callers that cannot allocate device memory -----------
-// Some callers may not allocate device memory at all: code recorded into a CUDA
-// graph (cudaMalloc cannot be captured), real-time or serving loops that must
-// not take cudaMalloc's implicit device synchronisation, and host programs whose
-// framework allocator already reserves all device memory.  For them,
+// Some callers may not allocate device memory at all: real-time or serving
+// loops that must not take cudaMalloc's implicit device synchronisation, and
+// host programs whose framework allocator already reserves all device memory
+// (a second allocator would fail or fragment it).  For them,
 // qsvm_kernel_batch_noalloc keeps the batch scratch (job table + work-queue
 // head) in a fixed array that lives in this library's device image instead of a
 // caller workspace.  The array is loaded with the library on every GPU that uses
@@ -832,10 +836,7 @@ namespace {
 
 constexpr int32_t kNoAllocMaxJobs = 1024;
 constexpr size_t kNoAllocBytes = 76 * 1024;  // >= the workspace of 1024 jobs
-static_assert(((256 + 64 * (size_t)kNoAllocMaxJobs + 255) / 256 * 256 + 8 * (size_t)(kNoAllocMaxJobs + 1) + 255) /
-                      256 * 256 <=
-                  kNoAllocBytes,
-              "static batch scratch too small for its job limit");
+static_assert(ws_total(kNoAllocMaxJobs) <= kNoAllocBytes, "static batch scratch too small for its job limit");
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
 

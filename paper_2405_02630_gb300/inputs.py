@@ -79,3 +79,18 @@ def batch_jobs(seed: int = 3, n_jobs: int = 32, qubits=(16, 64, 128, 256, 512, 7
         N = int(rng.integers(n_min, n_max + 1))
         jobs.append((rng.random((N, n)) * PI, n))
     return jobs
+
+
+def near_duplicate_clusters(n_base: int, copies: int, n_features: int, seed: int,
+                            frac: float = 0.05) -> tuple[np.ndarray, np.ndarray]:
+    """A Gram input rich in near-duplicate pairs: ``n_base`` MNIST-like rows, each with
+    ``copies`` - 1 perturbed copies (``near_duplicates`` with a different seed per copy),
+    all rows shuffled by a seeded permutation so that the copies of one base row land
+    both inside one tile of the Gram and in different tiles.  Returns (X, cluster) with
+    cluster[r] the base row that row r of X derives from."""
+    base = mnist_like_features(n_base, n_features, seed)
+    rows = [base] + [near_duplicates(base, seed + 1 + c, frac) for c in range(copies - 1)]
+    X = np.concatenate(rows, axis=0)
+    cluster = np.tile(np.arange(n_base), copies)
+    perm = np.random.default_rng(seed + 1000).permutation(X.shape[0])
+    return np.ascontiguousarray(X[perm]), cluster[perm]

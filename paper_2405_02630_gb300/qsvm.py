@@ -141,6 +141,17 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _optional_out(out, shape, **kw):
+    """An optional float64 output argument: True allocates one, False or None means
+    none, a tensor is used as given."""
+    import torch
+    if out is True:
+        return torch.empty(shape, dtype=torch.float64, **kw)
+    if out is False or out is None:
+        return None
+    return out
+
+
 # ---------------------------------------------------------------- queries ---
 def qsvm_mps_record_bytes(reps: int, precision) -> int:
     return int(lib().qsvm_mps_record_bytes(reps, _prec(precision)))
@@ -210,7 +221,7 @@ def qsvm_kernel_gram(mps, n_points: int, n_qubits: int, reps: int, precision, K=
     dev = device or mps.device
     if K is None:
         K = torch.empty((n_points, n_points), dtype=torch.float64, device=dev)
-    L = torch.empty((n_points, n_points), dtype=torch.float64, device=dev) if logK is True else (logK or None)
+    L = _optional_out(logK, (n_points, n_points), device=dev)
     _check(lib().qsvm_kernel_gram(_ptr(mps), n_points, n_qubits, reps, _prec(precision), _ptr(K), K.stride(0),
                                   _ptr(L), L.stride(0) if L is not None else 0, _stream(stream)))
     return K, L
@@ -231,7 +242,7 @@ def qsvm_kernel_cross(mps_a, n_a: int, mps_b, n_b: int, n_qubits: int, reps: int
     dev = mps_a.device
     if K is None:
         K = torch.empty((n_a, n_b), dtype=torch.float64, device=dev)
-    L = torch.empty((n_a, n_b), dtype=torch.float64, device=dev) if logK is True else (logK or None)
+    L = _optional_out(logK, (n_a, n_b), device=dev)
     _check(lib().qsvm_kernel_cross(_ptr(mps_a), n_a, _ptr(mps_b), n_b, n_qubits, reps, _prec(precision), _ptr(K),
                                    K.stride(0), _ptr(L), L.stride(0) if L is not None else 0, _stream(stream)))
     return K, L
@@ -402,18 +413,20 @@ def qsvm_gram_host_workspace_bytes(n_points: int, n_qubits: int, reps: int, prec
     return int(lib().qsvm_gram_host_workspace_bytes(n_points, n_qubits, reps, _prec(precision), int(bool(with_logk))))
 
 
-def gram_host(X, reps: int, precision, K=None, logK=False, ws=None, stream=None):
+def gram_host(X, reps: int, precision, K=None, logK=True, ws=None, stream=None):
     """The Gram of host data through qsvm_gram_host.  X: contiguous CPU float64 tensor
     (page-locked for asynchronous copies); K, logK: CPU float64 outputs (page-locked ones
-    are allocated if not given); ws: device scratch (allocated if not given).  Returns
-    (K, logK or None), complete once `stream` (default: the current stream) is synchronised."""
+    are allocated if not given; logK=False skips ln K); ws: device scratch (allocated if
+    not given).  Returns (K, logK or None), complete once `stream` (default: the current
+    stream) is synchronised.  ln K is returned by default: at hundreds of qubits almost
+    every off-diagonal K underflows to 0 in FP64 while ln K stays exact."""
     import torch
     if X.device.type != "cpu" or X.dtype != torch.float64 or not X.is_contiguous():
         raise ValueError("X must be a contiguous CPU float64 tensor")
     N, n = X.shape
     if K is None:
         K = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
-    L = torch.empty((N, N), dtype=torch.float64, pin_memory=True) if logK is True else (logK or None)
+    L = _optional_out(logK, (N, N), pin_memory=True)
     need = qsvm_gram_host_workspace_bytes(N, n, reps, precision, L is not None)
     if ws is None:
         ws = torch.empty(need, dtype=torch.uint8, device="cuda")
@@ -427,10 +440,10 @@ def qsvm_cross_host_workspace_bytes(n_a: int, n_b: int, n_qubits: int, reps: int
     return int(lib().qsvm_cross_host_workspace_bytes(n_a, n_b, n_qubits, reps, _prec(precision), int(bool(with_logk))))
 
 
-def cross_host(X_test, X_train, reps: int, precision, K=None, logK=False, ws=None, stream=None):
+def cross_host(X_test, X_train, reps: int, precision, K=None, logK=True, ws=None, stream=None):
     """Test x train kernel of host data through qsvm_cross_host (contiguous CPU float64
-    inputs; page-locked outputs allocated if not given).  Returns (K, logK or None), complete
-    once `stream` is synchronised."""
+    inputs; page-locked outputs allocated if not given; ln K unless logK=False).  Returns
+    (K, logK or None), complete once `stream` is synchronised."""
     import torch
     for X in (X_test, X_train):
         if X.device.type != "cpu" or X.dtype != torch.float64 or not X.is_contiguous():
@@ -439,7 +452,7 @@ def cross_host(X_test, X_train, reps: int, precision, K=None, logK=False, ws=Non
     nb = X_train.shape[0]
     if K is None:
         K = torch.empty((na, nb), dtype=torch.float64, pin_memory=True)
-    L = torch.empty((na, nb), dtype=torch.float64, pin_memory=True) if logK is True else (logK or None)
+    L = _optional_out(logK, (na, nb), pin_memory=True)
     need = qsvm_cross_host_workspace_bytes(na, nb, n, reps, precision, L is not None)
     if ws is None:
         ws = torch.empty(need, dtype=torch.uint8, device="cuda")
@@ -448,14 +461,17 @@ def cross_host(X_test, X_train, reps: int, precision, K=None, logK=False, ws=Non
     return K, L
 
 
-def gram(X, reps: int, precision, logK: bool = False, stream=None):
-    """Build the MPS of every row of X and return its Gram (K, logK or None)."""
+def gram(X, reps: int, precision, logK: bool = True, stream=None):
+    """Build the MPS of every row of X and return its Gram (K, logK), or (K, None) with
+    logK=False.  ln K is the default output: at hundreds of qubits K itself underflows
+    to 0 off the diagonal (kernel concentration) while ln K keeps the information."""
     N, n = X.shape
     mps = qsvm_build_mps(X, reps, precision, stream=stream)
     return qsvm_kernel_gram(mps, N, n, reps, precision, logK=logK, stream=stream)
 
 
-def cross(X_test, X_train, reps: int, precision, logK: bool = False, stream=None):
+def cross(X_test, X_train, reps: int, precision, logK: bool = True, stream=None):
+    """Test x train kernel of two feature matrices (K, logK), or (K, None) with logK=False."""
     ma = qsvm_build_mps(X_test, reps, precision, stream=stream)
     mb = qsvm_build_mps(X_train, reps, precision, stream=stream)
     return qsvm_kernel_cross(ma, X_test.shape[0], mb, X_train.shape[0], X_test.shape[1], reps, precision, logK=logK,

@@ -103,7 +103,7 @@ def gather_gram(K_local, n_points: int, reps: int, precision, dst=0, group=None,
     return K, (_mirror_upper(out[1], n_points) if ch == 2 else None)
 
 
-def gram_sharded(X, reps: int, precision, dst=0, group=None, logK: bool = False, stream=None):
+def gram_sharded(X, reps: int, precision, dst=0, group=None, logK: bool = True, stream=None):
     """The Gram of X (CUDA float64, n_points x n_qubits, every rank the same X) computed by
     all ranks of `group` together and gathered to `dst` (None: to every rank).  Each rank
     builds the MPS of all points, contracts its partition of the pair tiles, and takes part

@@ -37,13 +37,16 @@ def test_gram_host_matches_device(q, prec, N, n, reps):
 
 
 def test_gram_host_pageable_and_default_buffers(q):
-    """Pageable X, library-allocated pinned K: same bits as the device path."""
+    """Pageable X, library-allocated pinned K and ln K (the default): same bits as the
+    device path; logK=False returns no ln K."""
     N, n = 150, 20
     X = inputs.mnist_like_features(N, n, 77)
-    Kd, _ = q.gram(torch.from_numpy(X).cuda(), 2, "fp32_split")
+    Kd, Ld = q.gram(torch.from_numpy(X).cuda(), 2, "fp32_split")
     K, L = q.gram_host(torch.from_numpy(X), 2, "fp32_split")
+    K2, L2 = q.gram_host(torch.from_numpy(X), 2, "fp32_split", logK=False)
     torch.cuda.synchronize()
-    assert L is None and torch.equal(K, Kd.cpu())
+    assert torch.equal(K, Kd.cpu()) and torch.equal(L, Ld.cpu())
+    assert L2 is None and torch.equal(K2, Kd.cpu())
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_split", "fp32"])

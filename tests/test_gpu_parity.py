@@ -290,6 +290,32 @@ def test_near_duplicates_n784(q, oracle, prec):
     assert err <= tol, f"{prec}: max|dK| = {err:.3e}"
 
 
+@pytest.mark.parametrize("prec,reps", [("fp64", 2), ("fp32_split", 2), ("fp32_split", 3)])
+def test_gram_near_duplicate_clusters_n784(q, oracle, prec, reps):
+    """The symmetric Gram kernel (not the cross kernel) where |dK| <= 1e-6 bites: 24
+    MNIST-like base rows with three perturbed copies each, shuffled, so that pairs with
+    K in (0.1, 1) fall inside diagonal tiles (the kernel's masked half tile and mirror)
+    and in off-diagonal tiles.  Every entry against the oracle, ln K where K > 1e-300,
+    and the mirror bit-exact."""
+    X, cl = inputs.near_duplicate_clusters(24, 4, 784, 40)
+    N = X.shape[0]
+    td = q.qsvm_gram_tile_dim(reps, prec)
+    assert N > 2 * td
+    Ko, LKo = oracle.mps_gram(X, reps)
+    I, J = np.triu_indices(N, 1)
+    big = Ko[I, J] > 0.1
+    same_tile = (I // td) == (J // td)
+    assert (big & same_tile).sum() >= 5 and (big & ~same_tile).sum() >= 20
+    K, LK = q.gram(_dev(X), reps, prec, logK=True)
+    Kg, LKg = K.cpu().numpy(), LK.cpu().numpy()
+    assert q.qsvm_device_status() == 0
+    assert np.array_equal(Kg, Kg.T) and np.array_equal(LKg, LKg.T)
+    _check(Kg, Ko, prec, f"near-duplicate Gram reps={reps}", LKg, LKo)
+    # the informative entries on their own, in both kinds of tile
+    for m in (big & same_tile, big & ~same_tile):
+        assert np.max(np.abs(Kg[I[m], J[m]] - Ko[I[m], J[m]])) <= TOL[prec]
+
+
 def test_reps3_n784_logk(q, oracle):
     X = inputs.mnist_like_features(6, 784, 31)
     Ko, LKo = oracle.mps_gram(X, 3)

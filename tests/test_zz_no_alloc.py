@@ -1,11 +1,14 @@
 """qsvm_kernel_batch_noalloc: the batch launch for callers that cannot allocate
-device memory (graph-recorded code, serving loops that must not synchronise the
-device through cudaMalloc, hosts whose allocator owns all device memory).
+device memory (serving loops that must not synchronise the device through
+cudaMalloc, hosts whose framework allocator owns all device memory).
 
 Its scratch is a fixed array inside the library, reused by every call, so the
-test makes two calls in a row with different job sets through the C ABI and
-checks each against the workspace entry point qsvm_kernel_batch.  This file is
-collected last and needs nothing from the other test files.
+test makes two calls in a row with different job sets through the C ABI.  Each
+call runs the same persistent kernel on the same records as the workspace entry
+point qsvm_kernel_batch, so K and ln K must be bit-identical to it (a stale or
+partly rewritten job table would show); each job's K is also checked against the
+CPU oracle element by element.  This file is collected last and needs nothing from
+the other test files.
 """
 import ctypes
 
@@ -15,18 +18,19 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-6  # split-FP32 tolerance used by the parity tests
+TOL = 1e-6  # split-FP32 tolerance of the parity tests
+LOG_TOL = 1e-5
 
 
 def _make_jobs(qsvm, specs, reps, prec, seed):
     rng = np.random.default_rng(seed)
     jobs = []
     for N, n in specs:
-        X = torch.from_numpy(rng.random((N, n)) * np.pi).cuda()
-        mps = qsvm.qsvm_build_mps(X, reps, prec)
+        Xh = rng.random((N, n)) * np.pi
+        mps = qsvm.qsvm_build_mps(torch.from_numpy(Xh).cuda(), reps, prec)
         K = torch.full((N, N), float("nan"), dtype=torch.float64, device="cuda")
         L = torch.full((N, N), float("nan"), dtype=torch.float64, device="cuda")
-        jobs.append({"mps": mps, "n_points": N, "n_qubits": n, "K": K, "logK": L})
+        jobs.append({"mps": mps, "n_points": N, "n_qubits": n, "K": K, "logK": L, "X": Xh})
     return jobs
 
 
@@ -38,7 +42,7 @@ def _reference(qsvm, jobs, reps, prec):
     return ref
 
 
-def test_noalloc_batch_matches_workspace_batch_twice():
+def test_noalloc_batch_matches_workspace_batch_twice(oracle):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2405_02630_gb300 import qsvm
@@ -54,11 +58,14 @@ def test_noalloc_batch_matches_workspace_batch_twice():
         assert rc == qsvm.QSVM_OK, lib.qsvm_last_error().decode()
         torch.cuda.synchronize()
         for j, r in zip(jobs, ref):
-            assert not torch.isnan(j["K"]).any()
-            assert float((j["K"] - r["K"]).abs().max()) <= TOL
-            fin = torch.isfinite(r["logK"])
-            assert torch.equal(fin, torch.isfinite(j["logK"]))
-            assert float((j["logK"][fin] - r["logK"][fin]).abs().max()) <= 1e-5
+            assert not torch.isnan(j["K"]).any() and not torch.isnan(j["logK"]).any()
+            assert torch.equal(j["K"], r["K"])
+            assert torch.equal(j["logK"], r["logK"])  # -inf where K underflows, on both sides
+            Ko, LKo = oracle.mps_gram(j["X"], reps)
+            Kg, LKg = j["K"].cpu().numpy(), j["logK"].cpu().numpy()
+            assert np.max(np.abs(Kg - Ko)) <= TOL
+            m = Ko > 1e-300
+            assert np.max(np.abs(LKg[m] - LKo[m])) <= LOG_TOL
     assert qsvm.qsvm_device_status() == 0
 
 
