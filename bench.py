@@ -326,7 +326,7 @@ def run_ours(args):
     # pipeline shape: the autotuner times every shape on a Gram of up to 4096 of the
     # workload's points (untimed setup) and keeps the fastest for the timed steps
     pipeline = {"autotuned": False}
-    if args.autotune:
+    if not args.no_autotune:
         Nt = min(N, 4096)
         mps_t = torch.empty(qsvm.qsvm_mps_bytes(n, reps, Nt, P), dtype=torch.uint8, device=dev)
         qsvm.qsvm_build_mps(Xd[:Nt].contiguous(), reps, P, mps=mps_t, stream=stream)
@@ -340,6 +340,10 @@ def run_ours(args):
     pipeline["config"] = cfg
     if cfg >= 0:
         pipeline["sites_per_chunk"], pipeline["stages"] = qsvm.qsvm_config_info(cfg, reps, P)
+    side, tpp = qsvm.qsvm_config_tile(cfg, reps, P)
+    pipeline["cta_pairs"] = f"{side}x{side}"
+    pipeline["threads_per_pair"] = tpp
+    pipeline["configs_searched"] = qsvm.qsvm_num_configs() if pipeline["autotuned"] else 0
 
     LK = LKx = None  # ln K outputs, allocated for the timing with ln K written
 
@@ -743,8 +747,9 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the accuracy, FP64 and CPU side measurements")
     ap.add_argument("--sampled-fp64", action="store_true",
                     help="time the FP64 comparison path on the first 1/64 of the Gram's tiles only")
-    ap.add_argument("--autotune", action="store_true",
-                    help="pick the pipeline shape with the autotuner (on up to 4096 points) before timing")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (by default it picks the pipeline shape and the pairs per CTA on up "
+                         "to 4096 of the workload's points before timing)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

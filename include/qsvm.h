@@ -297,7 +297,8 @@ int32_t qsvm_kernel_batch_noalloc(const qsvm_job* jobs, int32_t n_jobs, int32_t 
 
 /* ---- pipeline configurations and the autotuner ----------------------------
  * The pair kernels stream site records through shared memory in chunks; a
- * configuration fixes the bytes per point and chunk and the stages in flight.
+ * configuration fixes the bytes per point and chunk, the stages in flight, and
+ * whether a CTA contracts a whole tile of pairs or a quarter of one.
  * Results are bit-identical for every configuration (the arithmetic and its
  * order do not depend on it); only speed differs.  The selection is per
  * (reps, precision), process-wide, and used by every later launch. */
@@ -305,6 +306,16 @@ int32_t qsvm_num_configs(void);
 /* sites per chunk and stages of configuration `index` for (reps, precision) */
 int32_t qsvm_config_info(int32_t index, int32_t reps, int32_t precision, int32_t* sites_per_chunk,
                          int32_t* stages);
+/* qsvm_config_tile -- the block of pairs one CTA contracts under configuration
+ * `index` (-1: the default) for (reps, precision): *pairs_per_side x *pairs_per_side
+ * pairs with *threads_per_pair threads each (either output nullable).  The first
+ * qsvm_num_configs()/2 configurations give each CTA a whole tile of
+ * qsvm_gram_tile_dim() pairs per side, the others a quarter of one; tile indices,
+ * partitions and tile lists are the same for both (they count whole tiles), and
+ * the batch launches always use whole tiles.  Errors: QSVM_ERR_ARG for an index
+ * out of range, QSVM_ERR_CHI for reps outside 1..3. */
+int32_t qsvm_config_tile(int32_t index, int32_t reps, int32_t precision, int32_t* pairs_per_side,
+                         int32_t* threads_per_pair);
 int32_t qsvm_set_config(int32_t reps, int32_t precision, int32_t index); /* index -1: default */
 int32_t qsvm_get_config(int32_t reps, int32_t precision);
 /* qsvm_autotune -- times the Gram of `mps` (n_points, n_qubits) under every

@@ -1,4 +1,5 @@
-"""Autotuner front end: picks the pipeline configuration of the pair kernels per
+"""Autotuner front end: picks the pipeline configuration of the pair kernels (sites
+per chunk, stages in flight, and a whole or a quarter tile of pairs per CTA) per
 (device, reps, precision, qubit-count bucket) and remembers it across processes.
 
 The timing itself is native (qsvm_autotune in libqsvm times every configuration
@@ -58,7 +59,8 @@ def tune(mps, n_points: int, n_qubits: int, reps: int, precision, K, stream=None
     """Times every configuration on this Gram (K is overwritten), selects the fastest."""
     best, ms = qsvm.qsvm_autotune(mps, n_points, n_qubits, reps, precision, K, stream=stream)
     rec = {"config": best, "ms": ms, "n_points": n_points,
-           "shape": qsvm.qsvm_config_info(best, reps, precision)}
+           "shape": qsvm.qsvm_config_info(best, reps, precision),
+           "cta": qsvm.qsvm_config_tile(best, reps, precision)}
     if save:
         d = _load()
         d[_key(reps, precision, n_qubits)] = rec

@@ -14,6 +14,9 @@ struct PipeShape {
 static const PipeShape kShapes[] = {{512, 4},  {1024, 3}, {512, 3},  {1024, 2}, {1024, 4},  {2048, 2},
                                     {2048, 3}, {512, 2},  {1152, 2}, {1440, 2}, {2304, 2}, {3456, 2}};
 constexpr int kNumShapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+// Configurations: shape c % kNumShapes with whole tiles per CTA (c < kNumShapes)
+// or a quarter tile per CTA (c >= kNumShapes).
+constexpr int kNumSubs = 2;
 
 // Defaults from shape sweeps on one GB300 (n = 784 Grams): split FP32 with 64-byte
 // gauged records, two stages of 22 sites at reps = 2 and of 32 sites at reps = 3
@@ -28,10 +31,16 @@ int default_shape(int chi, int prec) {
   return (prec == QSVM_FP32 || chi >= 8) ? 3 : 1;
 }
 
-int num_pipe_shapes() { return kNumShapes; }
+int num_pipe_shapes() { return kNumShapes * kNumSubs; }
 
-PipeCfg make_pipe(int chi, int prec, int shape) {
-  if (shape < 0 || shape >= kNumShapes) shape = default_shape(chi, prec);
+PipeCfg make_pipe(int chi, int prec, int config) {
+  int shape = config, sub = 1;
+  if (config < 0 || config >= kNumShapes * kNumSubs) {
+    shape = default_shape(chi, prec);
+  } else {
+    shape = config % kNumShapes;
+    sub = 1 + config / kNumShapes;
+  }
   const int rec = (int)record_bytes(chi, prec);
   PipeCfg pc;
   pc.S = kShapes[shape].chunk_bytes >= rec ? kShapes[shape].chunk_bytes / rec : 1;
@@ -43,29 +52,42 @@ PipeCfg make_pipe(int chi, int prec, int shape) {
   // bytes, sends all 16 lanes to one group).
   pc.slot_bytes = pc.S * rec;
   if ((pc.slot_bytes / 16) % 2 == 0) pc.slot_bytes += 16;
-  pc.stage_bytes = 2 * tile_side(chi, prec) * pc.slot_bytes;
+  pc.sub = sub;
+  pc.tile = tile_side(chi, prec) / sub;
+  pc.stage_bytes = 2 * pc.tile * pc.slot_bytes;
   return pc;
+}
+
+// The persistent batch kernel always contracts whole tiles: the same shape with sub = 1.
+PipeCfg whole_tile_pipe(int chi, int prec, int config) {
+  return make_pipe(chi, prec, (config < 0 || config >= kNumShapes * kNumSubs) ? -1 : config % kNumShapes);
 }
 
 int pipe_smem(const PipeCfg& pc, int chi, int prec) { return pipe_smem_bytes(pc, chi, prec); }
 
-template <int CHI, int PREC>
-static cudaError_t launch_pair_t(const TileArgs& a, int64_t ntiles, const PipeCfg& pc, cudaStream_t st) {
-  auto kern = pair_tile_kernel<CHI, PREC>;
+template <int CHI, int PREC, int SUB>
+static cudaError_t launch_pair_sub(const TileArgs& a, int64_t ntiles, const PipeCfg& pc, cudaStream_t st) {
+  auto kern = pair_tile_kernel<CHI, PREC, SUB>;
   const int smem = pipe_smem_bytes(pc, CHI, PREC);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  const int64_t per_launch = (int64_t)INT_MAX / (SUB * SUB);  // tiles per launch: grid = SUB^2 x tiles
   int64_t done = 0;
   while (done < ntiles) {
-    const int64_t cnt = (ntiles - done) < (int64_t)INT_MAX ? (ntiles - done) : (int64_t)INT_MAX;
+    const int64_t cnt = (ntiles - done) < per_launch ? (ntiles - done) : per_launch;
     TileArgs b = a;
     b.tile_begin = a.tile_begin + done;
-    kern<<<(unsigned)cnt, kTileThreads, smem, st>>>(b, pc);
+    kern<<<(unsigned)(cnt * SUB * SUB), kernel_threads<CHI, PREC, SUB>(), smem, st>>>(b, pc);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     done += cnt;
   }
   return cudaSuccess;
+}
+
+template <int CHI, int PREC>
+static cudaError_t launch_pair_t(const TileArgs& a, int64_t ntiles, const PipeCfg& pc, cudaStream_t st) {
+  return pc.sub == 2 ? launch_pair_sub<CHI, PREC, 2>(a, ntiles, pc, st) : launch_pair_sub<CHI, PREC, 1>(a, ntiles, pc, st);
 }
 
 // Sets the kernel's shared-memory attribute and sizes its grid (SMs x resident
@@ -80,7 +102,9 @@ static cudaError_t prepare_persistent_t(const PipeCfg& pc, int64_t total_tiles, 
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kernel_threads<CHI, PREC, 1>(), smem)) !=
+      cudaSuccess)
+    return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > total_tiles) grid = total_tiles;
@@ -90,7 +114,8 @@ static cudaError_t prepare_persistent_t(const PipeCfg& pc, int64_t total_tiles, 
 
 template <int CHI, int PREC>
 static cudaError_t launch_persistent_t(const BatchArgs& a, const PipeCfg& pc, int grid, cudaStream_t st) {
-  pair_persistent_kernel<CHI, PREC><<<(unsigned)grid, kTileThreads, pipe_smem_bytes(pc, CHI, PREC), st>>>(a, pc);
+  pair_persistent_kernel<CHI, PREC><<<(unsigned)grid, kernel_threads<CHI, PREC, 1>(), pipe_smem_bytes(pc, CHI, PREC),
+                                      st>>>(a, pc);
   return cudaGetLastError();
 }
 
@@ -146,6 +171,7 @@ cudaError_t launch_persistent(int chi, int prec, const BatchArgs& a, const PipeC
 }
 
 int pair_tile_dim(int chi, int prec) { return tile_side(chi, prec); }
+int pair_threads(int chi, int prec) { return threads_per_pair(chi, prec); }
 
 cudaError_t pair_status(cudaStream_t st, int clear, int32_t* out) {
   int32_t v = 0;

@@ -1321,28 +1321,38 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
   }
 };
 
-constexpr int kTileThreads = 256;      // every tile kernel runs 256 threads
-constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kMaxStages = 4;
 constexpr int kCtlBytes = 128;
 
-// Tile geometry: one thread per pair on a 16 x 16 tile, except split FP32 at
-// chi = 8, which runs four threads per pair on an 8 x 8 tile (QuadEngine).
+// Tile geometry.  The Gram and cross kernels are cut into tiles of tile_side x
+// tile_side pairs (16 x 16; 8 x 8 for split FP32 at chi = 8, which runs four threads
+// per pair, QuadEngine); tile indices, partitions and tile lists use this side.  A
+// CTA contracts either a whole tile or, with a sub-tile configuration, one of its
+// 2 x 2 quarters (8 x 8 or 4 x 4 pairs), so a launch runs 4 CTAs per tile; the
+// pipeline configuration picks which (an autotuner knob).
 __host__ __device__ constexpr int threads_per_pair(int chi, int prec) {
   return (chi >= 8 && prec == QSVM_FP32_SPLIT) ? 4 : 1;
 }
 __host__ __device__ constexpr int tile_side(int chi, int prec) { return threads_per_pair(chi, prec) == 4 ? 8 : 16; }
+// threads of a CTA that contracts a ti x ti block of pairs with tpp threads per pair
+__host__ __device__ constexpr int cta_threads(int ti, int tpp) { return ti * ti * tpp; }
 __host__ __device__ constexpr int out_bytes(int ti) { return ti * (ti + 1) * 16; }
 // shared environment buffer of the four-thread layout: 32 entries x 16 B per pair,
 // padded to 36 entries (a stride of 4 mod 8 sixteen-byte bank groups)
 constexpr int kQuadPairFloats = 32 * 4;  // the four-thread engine's exchange buffer per pair
-__host__ __device__ constexpr int ebuf_bytes(int chi, int prec) {
-  return threads_per_pair(chi, prec) == 4 ? (kTileThreads / 4) * kQuadPairFloats * 4 : 0;
+__host__ __device__ constexpr int ebuf_bytes(int chi, int prec, int ti) {
+  return threads_per_pair(chi, prec) == 4 ? ti * ti * kQuadPairFloats * 4 : 0;
 }
 
-template <int CHI, int PREC>
+// CTAs per SM the register budget is set for; a sub-tile CTA (SUB = 2) has a
+// quarter of the threads, so four times as many keep the same warps resident
+template <int CHI, int PREC, int SUB>
 __host__ __device__ constexpr int min_blocks_per_sm() {
-  return (threads_per_pair(CHI, PREC) == 4) ? 2 : (CHI >= 8) ? 1 : ((PREC == QSVM_FP32) ? 3 : 2);
+  return SUB * SUB * ((threads_per_pair(CHI, PREC) == 4) ? 2 : (CHI >= 8) ? 1 : ((PREC == QSVM_FP32) ? 3 : 2));
+}
+template <int CHI, int PREC, int SUB>
+__host__ __device__ constexpr int kernel_threads() {
+  return cta_threads(tile_side(CHI, PREC) / SUB, threads_per_pair(CHI, PREC));
 }
 
 // Shared-memory control block at the end of the dynamic allocation.
@@ -1357,7 +1367,7 @@ static_assert(sizeof(TileCtl) <= kCtlBytes, "control block");
 
 // Dynamic shared memory: stages | output tile (K, logK) | control block | environment buffer (4-thread layout)
 __host__ __device__ inline int pipe_smem_bytes(const PipeCfg& pc, int chi, int prec) {
-  return pc.stages * pc.stage_bytes + out_bytes(tile_side(chi, prec)) + kCtlBytes + ebuf_bytes(chi, prec);
+  return pc.stages * pc.stage_bytes + out_bytes(pc.tile) + kCtlBytes + ebuf_bytes(chi, prec, pc.tile);
 }
 
 // What one tile needs to know.
@@ -1390,12 +1400,14 @@ struct EngineFor<CHI, PREC, 4> {
   using type = QuadEngine<PREC>;
 };
 
-template <int CHI, int PREC>
+// TI is the side of the block of pairs this CTA contracts (a tile or a sub-tile);
+// w.ti and w.tj count in units of TI.
+template <int CHI, int PREC, int TI>
 __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, uint8_t* smem, TileCtl* ctl,
                                          int& gchunk) {
   using Rec = Record<CHI, PREC>;
   constexpr int TPP = threads_per_pair(CHI, PREC);
-  constexpr int TI = tile_side(CHI, PREC);
+  constexpr int kWarps = cta_threads(TI, TPP) / 32;
   using Eng = typename EngineFor<CHI, PREC, TPP>::type;
   const int S = pc.S, NST = pc.stages, SLOT = pc.slot_bytes, STAGE = pc.stage_bytes;
   double* outK = reinterpret_cast<double*>(smem + NST * STAGE);
@@ -1497,7 +1509,7 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
     int last = 0;
     if (lane == 0) {
       __threadfence_block();
-      last = atomicAdd(&ctl->done[st], 1) == kTileWarps - 1;
+      last = atomicAdd(&ctl->done[st], 1) == kWarps - 1;
       if (last) ctl->done[st] = 0;
     }
     last = __shfl_sync(0xffffffffu, last, 0);
@@ -1555,9 +1567,8 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
   return true;
 }
 
-template <int CHI, int PREC>
 __device__ __forceinline__ TileCtl* tile_ctl(uint8_t* smem, const PipeCfg& pc) {
-  return reinterpret_cast<TileCtl*>(smem + pc.stages * pc.stage_bytes + out_bytes(tile_side(CHI, PREC)));
+  return reinterpret_cast<TileCtl*>(smem + pc.stages * pc.stage_bytes + out_bytes(pc.tile));
 }
 
 __device__ __forceinline__ void tile_ctl_init(TileCtl* ctl, const PipeCfg& pc) {
@@ -1573,17 +1584,30 @@ __device__ __forceinline__ void tile_ctl_init(TileCtl* ctl, const PipeCfg& pc) {
   __syncthreads();
 }
 
-// One CTA per tile of a launch (grid = number of tiles in [tile_begin, ...)).
-template <int CHI, int PREC>
-__global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>()))
+// One CTA per tile of a launch (grid = number of tiles in [tile_begin, ...)), or,
+// with SUB = 2, one CTA per quarter of a tile (grid = 4 x tiles): CTA 4t + 2qi + qj
+// takes quarter (qi, qj) of tile t.  In a diagonal tile of a Gram the quarter
+// (1, 0) lies below the diagonal (its entries are the mirror of quarter (0, 1)),
+// and quarters beyond a ragged last tile row or column hold no pairs: such CTAs
+// return at once.
+template <int CHI, int PREC, int SUB>
+__global__ void __launch_bounds__(kernel_threads<CHI, PREC, SUB>(), (min_blocks_per_sm<CHI, PREC, SUB>()))
     pair_tile_kernel(TileArgs args, PipeCfg pc) {
-  uint8_t* smem = qsvm_dyn_smem;
-  TileCtl* ctl = tile_ctl<CHI, PREC>(smem, pc);
-  tile_ctl_init(ctl, pc);
-  const int64_t b = args.tile_begin + blockIdx.x;
+  constexpr int TI = tile_side(CHI, PREC) / SUB;
+  const int64_t b = args.tile_begin + blockIdx.x / (SUB * SUB);
+  const int qi = (int)(blockIdx.x % (SUB * SUB)) / SUB, qj = (int)(blockIdx.x % (SUB * SUB)) % SUB;
   TileWork w;
   if (args.symmetric) sym_tile_decode(b, args.tiles_j, w.ti, w.tj);
   else rect_tile_decode(b, args.tiles_i, args.tiles_j, w.ti, w.tj);
+  if (SUB > 1) {
+    if (args.symmetric && w.ti == w.tj && qi > qj) return;
+    w.ti = w.ti * SUB + qi;
+    w.tj = w.tj * SUB + qj;
+    if (w.ti * TI >= args.nA || w.tj * TI >= args.nB) return;
+  }
+  uint8_t* smem = qsvm_dyn_smem;
+  TileCtl* ctl = tile_ctl(smem, pc);
+  tile_ctl_init(ctl, pc);
   w.mpsA = args.mpsA;
   w.mpsB = args.mpsB;
   w.nA = args.nA;
@@ -1595,18 +1619,18 @@ __global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>())
   w.logK = args.logK;
   w.ldl = args.ldl;
   int gchunk = 0;
-  run_tile<CHI, PREC>(w, pc, smem, ctl, gchunk);
+  run_tile<CHI, PREC, TI>(w, pc, smem, ctl, gchunk);
 }
 
 // Persistent kernel over a queue of Gram tiles from many jobs: every CTA pulls
 // the next tile index from a device counter until the queue is empty.  Jobs are
 // ordered heaviest first by the host; tile t belongs to the job j with
-// prefix[j] <= t < prefix[j + 1].
+// prefix[j] <= t < prefix[j + 1].  Always whole tiles (pc.tile == tile_side).
 template <int CHI, int PREC>
-__global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>()))
+__global__ void __launch_bounds__(kernel_threads<CHI, PREC, 1>(), (min_blocks_per_sm<CHI, PREC, 1>()))
     pair_persistent_kernel(BatchArgs args, PipeCfg pc) {
   uint8_t* smem = qsvm_dyn_smem;
-  TileCtl* ctl = tile_ctl<CHI, PREC>(smem, pc);
+  TileCtl* ctl = tile_ctl(smem, pc);
   tile_ctl_init(ctl, pc);
   int gchunk = 0;
   while (true) {
@@ -1635,7 +1659,7 @@ __global__ void __launch_bounds__(kTileThreads, (min_blocks_per_sm<CHI, PREC>())
     w.ldk = J.ldk;
     w.logK = J.logK;
     w.ldl = J.ldl;
-    if (!run_tile<CHI, PREC>(w, pc, smem, ctl, gchunk)) break;
+    if (!run_tile<CHI, PREC, tile_side(CHI, PREC)>(w, pc, smem, ctl, gchunk)) break;
   }
 }
 

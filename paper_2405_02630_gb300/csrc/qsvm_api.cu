@@ -18,6 +18,7 @@ cudaError_t launch_pair(int chi, int prec, const TileArgs& a, int64_t ntiles, co
 cudaError_t prepare_persistent(int chi, int prec, const PipeCfg& pc, int64_t total_tiles, int* grid_out);
 cudaError_t launch_persistent(int chi, int prec, const BatchArgs& a, const PipeCfg& pc, int grid, cudaStream_t st);
 int pair_tile_dim(int chi, int prec);
+int pair_threads(int chi, int prec);
 cudaError_t pair_status(cudaStream_t st, int clear, int32_t* out);
 int num_pipe_shapes();
 cudaError_t launch_wait_timeout_selftest(uint64_t limit_ns, cudaStream_t st);
@@ -34,7 +35,8 @@ cudaError_t launch_svc_fit(const double* K, int64_t ldk, const DevSvcProblem* pr
                            int64_t max_iter, double* b_out, int64_t* iters_out, cudaStream_t st);
 cudaError_t launch_svc_decision(const double* Kx, int64_t ldk, int64_t m, const DevSvcProblem* probs, int n_probs,
                                 const double* b, double* F, cudaStream_t st);
-PipeCfg make_pipe(int chi, int prec, int shape);
+PipeCfg make_pipe(int chi, int prec, int config);
+PipeCfg whole_tile_pipe(int chi, int prec, int config);
 int pipe_smem(const PipeCfg& pc, int chi, int prec);
 }  // namespace qsvm
 
@@ -82,6 +84,10 @@ size_t form_b_offset(int64_t n_points, int n_qubits, int reps, int prec) {
 std::atomic<int> g_config[3][3] = {{{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}, {{-1}, {-1}, {-1}}};
 
 PipeCfg current_pipe(int reps, int prec) { return make_pipe(1 << reps, prec, g_config[reps - 1][prec].load()); }
+// the batch (persistent) kernel: the selected shape, always whole tiles per CTA
+PipeCfg current_batch_pipe(int reps, int prec) {
+  return whole_tile_pipe(1 << reps, prec, g_config[reps - 1][prec].load());
+}
 
 constexpr int kMaxSmemPerCta = 227 * 1024;
 
@@ -574,7 +580,7 @@ int32_t qsvm_kernel_batch(const qsvm_job* jobs, int32_t n_jobs, int32_t reps, in
   cudaError_t e = cudaMemcpyAsync(ws, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "batch job table upload");
   const BatchArgs a = batch_args(ws, n_jobs, img.total_tiles);
-  const PipeCfg pc = current_pipe(reps, precision);
+  const PipeCfg pc = current_batch_pipe(reps, precision);
   int grid = 0;
   e = prepare_persistent(1 << reps, precision, pc, img.total_tiles, &grid);
   if (e == cudaSuccess) e = launch_persistent(1 << reps, precision, a, pc, grid, st);
@@ -600,7 +606,7 @@ int32_t qsvm_batch_plan_create(const qsvm_job* jobs, int32_t n_jobs, int32_t rep
     return cuda_fail(e, "capture stream");
   }
   const BatchArgs a = batch_args(ws, n_jobs, img.total_tiles);
-  const PipeCfg pc = current_pipe(reps, precision);
+  const PipeCfg pc = current_batch_pipe(reps, precision);
   int grid = 0;
   e = prepare_persistent(1 << reps, precision, pc, img.total_tiles, &grid);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
@@ -645,6 +651,17 @@ int32_t qsvm_config_info(int32_t index, int32_t reps, int32_t precision, int32_t
   const PipeCfg pc = make_pipe(1 << reps, precision, index);
   if (sites_per_chunk) *sites_per_chunk = pc.S;
   if (stages) *stages = pc.stages;
+  return QSVM_OK;
+}
+
+int32_t qsvm_config_tile(int32_t index, int32_t reps, int32_t precision, int32_t* pairs_per_side,
+                         int32_t* threads_per_pair_out) {
+  int32_t rc = check_common(2, reps, precision);
+  if (rc) return rc;
+  if (index < -1 || index >= num_pipe_shapes()) return fail(QSVM_ERR_ARG, "config index %d out of range", index);
+  const PipeCfg pc = make_pipe(1 << reps, precision, index);
+  if (pairs_per_side) *pairs_per_side = pc.tile;
+  if (threads_per_pair_out) *threads_per_pair_out = pair_threads(1 << reps, precision);
   return QSVM_OK;
 }
 
@@ -880,7 +897,7 @@ extern "C" int32_t qsvm_kernel_batch_noalloc(const qsvm_job* jobs, int32_t n_job
   cudaError_t e = cudaMemcpyAsync(ws, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "batch job table upload");
   const BatchArgs a = batch_args(ws, n_jobs, img.total_tiles);
-  const PipeCfg pc = current_pipe(reps, precision);
+  const PipeCfg pc = current_batch_pipe(reps, precision);
   int grid = 0;
   e = prepare_persistent(1 << reps, precision, pc, img.total_tiles, &grid);
   if (e == cudaSuccess) e = launch_persistent(1 << reps, precision, a, pc, grid, st);

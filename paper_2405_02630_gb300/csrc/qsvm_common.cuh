@@ -204,12 +204,15 @@ struct TileArgs {
 };
 
 // Runtime pipeline configuration of the pair kernels (the autotuner's knobs):
-// sites per chunk and number of shared-memory stages in flight.
+// sites per chunk, number of shared-memory stages in flight, and whether a CTA
+// contracts a whole tile or a quarter of one.
 struct PipeCfg {
   int S;            // sites per chunk
   int stages;       // 2..4
   int slot_bytes;   // S * record bytes, padded to an odd number of 16-byte units (per point per stage)
-  int stage_bytes;  // 2 * tile side points * slot_bytes
+  int stage_bytes;  // 2 * tile points * slot_bytes
+  int sub;          // 1: a CTA per tile; 2: a CTA per quarter tile
+  int tile;         // side of the block of pairs a CTA contracts (tile side / sub)
 };
 
 // One Gram job of a batch, as the persistent kernel reads it (64 bytes).

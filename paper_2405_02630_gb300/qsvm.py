@@ -79,6 +79,7 @@ _SIGS = {
     "qsvm_batch_plan_destroy": (_i32, [_vp]),
     "qsvm_num_configs": (_i32, []),
     "qsvm_config_info": (_i32, [_i32, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "qsvm_config_tile": (_i32, [_i32, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "qsvm_set_config": (_i32, [_i32, _i32, _i32]),
     "qsvm_get_config": (_i32, [_i32, _i32]),
     "qsvm_autotune": (_i32, [_vp, _i64, _i32, _i32, _i32, _dp, _i64, _vp, ctypes.POINTER(_i32),
@@ -316,6 +317,13 @@ def qsvm_config_info(index: int, reps: int, precision):
     s, st = _i32(0), _i32(0)
     _check(lib().qsvm_config_info(index, reps, _prec(precision), ctypes.byref(s), ctypes.byref(st)))
     return int(s.value), int(st.value)
+
+
+def qsvm_config_tile(index: int, reps: int, precision):
+    """(pairs per side, threads per pair) of the block one CTA contracts under `index`."""
+    a, b = _i32(), _i32()
+    _check(lib().qsvm_config_tile(index, reps, _prec(precision), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def qsvm_set_config(reps: int, precision, index: int):

@@ -156,6 +156,16 @@ def test_configs():
                 assert S >= 1 and 2 <= st <= 4
     S2, _ = qsvm.qsvm_config_info(1, 2, "fp32_split")
     assert S2 == 16  # 1 KB of 64-byte records per point and chunk
+    # the first half of the configurations give a CTA a whole tile, the second half a quarter
+    for reps, prec, side, tpp in ((1, "fp64", 16, 1), (2, "fp32_split", 16, 1), (3, "fp32_split", 8, 4),
+                                  (3, "fp64", 16, 1)):
+        assert qsvm.qsvm_gram_tile_dim(reps, prec) == side
+        assert qsvm.qsvm_config_tile(-1, reps, prec) == (side, tpp)
+        for c in range(n):
+            assert qsvm.qsvm_config_tile(c, reps, prec) == (side if c < n // 2 else side // 2, tpp)
+            assert qsvm.qsvm_config_info(c, reps, prec) == qsvm.qsvm_config_info(c % (n // 2), reps, prec)
+    with pytest.raises(qsvm.QsvmError):
+        qsvm.qsvm_config_tile(n, 2, "fp32_split")
     assert qsvm.qsvm_get_config(2, "fp64") == -1
     qsvm.qsvm_set_config(2, "fp64", 0)
     assert qsvm.qsvm_get_config(2, "fp64") == 0

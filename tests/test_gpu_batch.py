@@ -96,6 +96,38 @@ def test_every_config_bit_identical(q, reps):
     q.qsvm_set_config(reps, prec, -1)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_split", "fp32"])
+@pytest.mark.parametrize("reps", [1, 2, 3])
+def test_quarter_tile_configs_vs_oracle(q, oracle, prec, reps):
+    """Configurations that give each CTA a quarter of a tile: Gram and cross kernel with
+    ragged edges (quarters beyond the last row or column, the skipped quarter below a
+    diagonal tile) against the oracle, and bit-identical to the whole-tile default."""
+    tol = {"fp64": 1e-10, "fp32_split": 1e-6, "fp32": 2e-5}[prec]
+    n, N, Nt = 13, 37, 21
+    X, Xt = inputs.uniform_features(N, n, 61), inputs.uniform_features(Nt, n, 62)
+    Ko, _ = oracle.mps_gram(X, reps)
+    Kxo, _ = oracle.mps_cross(Xt, X, reps)
+    Xd, Xtd = torch.from_numpy(X).cuda(), torch.from_numpy(Xt).cuda()
+    q.qsvm_set_config(reps, prec, -1)
+    Kdef, Ldef = q.gram(Xd, reps, prec)
+    Kxdef, _ = q.cross(Xtd, Xd, reps, prec)
+    half = q.qsvm_num_configs() // 2
+    try:
+        for c in (half + 3, half + 9):
+            q.qsvm_set_config(reps, prec, c)
+            side, _ = q.qsvm_config_tile(c, reps, prec)
+            assert side == q.qsvm_gram_tile_dim(reps, prec) // 2
+            K, L = q.gram(Xd, reps, prec)
+            Kx, _ = q.cross(Xtd, Xd, reps, prec)
+            torch.cuda.synchronize()
+            assert q.qsvm_device_status() == 0
+            assert torch.equal(K, Kdef) and torch.equal(L, Ldef) and torch.equal(Kx, Kxdef)
+            assert float(np.max(np.abs(K.cpu().numpy() - Ko))) <= tol
+            assert float(np.max(np.abs(Kx.cpu().numpy() - Kxo))) <= tol
+    finally:
+        q.qsvm_set_config(reps, prec, -1)
+
+
 def test_autotune_selects_a_config(q, tmp_path, monkeypatch):
     from paper_2405_02630_gb300 import autotune
     monkeypatch.setenv("QSVM_AUTOTUNE_CACHE", str(tmp_path / "at.json"))
