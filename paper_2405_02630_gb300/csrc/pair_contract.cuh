@@ -1567,8 +1567,10 @@ __device__ __forceinline__ bool run_tile(const TileWork& w, const PipeCfg& pc, u
   return true;
 }
 
+// the control block of a CTA whose block of pairs has side TI (== pc.tile)
+template <int TI>
 __device__ __forceinline__ TileCtl* tile_ctl(uint8_t* smem, const PipeCfg& pc) {
-  return reinterpret_cast<TileCtl*>(smem + pc.stages * pc.stage_bytes + out_bytes(pc.tile));
+  return reinterpret_cast<TileCtl*>(smem + pc.stages * pc.stage_bytes + out_bytes(TI));
 }
 
 __device__ __forceinline__ void tile_ctl_init(TileCtl* ctl, const PipeCfg& pc) {
@@ -1594,20 +1596,25 @@ template <int CHI, int PREC, int SUB>
 __global__ void __launch_bounds__(kernel_threads<CHI, PREC, SUB>(), (min_blocks_per_sm<CHI, PREC, SUB>()))
     pair_tile_kernel(TileArgs args, PipeCfg pc) {
   constexpr int TI = tile_side(CHI, PREC) / SUB;
-  const int64_t b = args.tile_begin + blockIdx.x / (SUB * SUB);
-  const int qi = (int)(blockIdx.x % (SUB * SUB)) / SUB, qj = (int)(blockIdx.x % (SUB * SUB)) % SUB;
+  uint8_t* smem = qsvm_dyn_smem;
+  TileCtl* ctl = tile_ctl<TI>(smem, pc);
   TileWork w;
-  if (args.symmetric) sym_tile_decode(b, args.tiles_j, w.ti, w.tj);
-  else rect_tile_decode(b, args.tiles_i, args.tiles_j, w.ti, w.tj);
-  if (SUB > 1) {
+  if constexpr (SUB > 1) {
+    const int64_t b = args.tile_begin + blockIdx.x / (SUB * SUB);
+    const int qi = (int)(blockIdx.x % (SUB * SUB)) / SUB, qj = (int)(blockIdx.x % (SUB * SUB)) % SUB;
+    if (args.symmetric) sym_tile_decode(b, args.tiles_j, w.ti, w.tj);
+    else rect_tile_decode(b, args.tiles_i, args.tiles_j, w.ti, w.tj);
     if (args.symmetric && w.ti == w.tj && qi > qj) return;
     w.ti = w.ti * SUB + qi;
     w.tj = w.tj * SUB + qj;
     if (w.ti * TI >= args.nA || w.tj * TI >= args.nB) return;
+    tile_ctl_init(ctl, pc);
+  } else {
+    tile_ctl_init(ctl, pc);
+    const int64_t b = args.tile_begin + blockIdx.x;
+    if (args.symmetric) sym_tile_decode(b, args.tiles_j, w.ti, w.tj);
+    else rect_tile_decode(b, args.tiles_i, args.tiles_j, w.ti, w.tj);
   }
-  uint8_t* smem = qsvm_dyn_smem;
-  TileCtl* ctl = tile_ctl(smem, pc);
-  tile_ctl_init(ctl, pc);
   w.mpsA = args.mpsA;
   w.mpsB = args.mpsB;
   w.nA = args.nA;
@@ -1630,7 +1637,7 @@ template <int CHI, int PREC>
 __global__ void __launch_bounds__(kernel_threads<CHI, PREC, 1>(), (min_blocks_per_sm<CHI, PREC, 1>()))
     pair_persistent_kernel(BatchArgs args, PipeCfg pc) {
   uint8_t* smem = qsvm_dyn_smem;
-  TileCtl* ctl = tile_ctl(smem, pc);
+  TileCtl* ctl = tile_ctl<tile_side(CHI, PREC)>(smem, pc);
   tile_ctl_init(ctl, pc);
   int gchunk = 0;
   while (true) {
