@@ -65,6 +65,14 @@ enum qsvm_precision {
    * FP32 FMAs, and the lo terms carried as FP32 corrections.  Accuracy near
    * FP64 (|dK| ~ 1e-8 at n = 784) at FP32-pipe speed. */
   QSVM_FP32_SPLIT = 2
+  /* There is no tensor-core value.  TF32 operands (|dK| ~ 0.25 at n = 784) and
+   * two-term BF16 operands (~3e-3) miss the 1e-6 bar outright (CPU emulation of
+   * the arithmetic).  Three-term TF32 operands with FP32 accumulation would meet
+   * it, but the only products with an operand shared across pairs are 2 x 2
+   * complex (one m16n8k4 MMA per 4 pairs) and the pairs must be regrouped through
+   * shared memory twice per site: on GB300 a kernel doing only those MMAs, the
+   * operand re-splits and the regrouping ran at 4.2e7 entries/s at n = 784,
+   * reps = 2, against 8.0e7 for the complete QSVM_FP32_SPLIT contraction. */
 };
 
 /* ---- MPS storage ---------------------------------------------------------
