@@ -4,8 +4,8 @@
 Workload (default): n = 784 qubits (28 x 28 MNIST-like features, 80 % exact zeros,
 the rest uniform on (0, 1] * pi; seed 4), reps = 2 (bond dimension 4),
 N = 8192 points, the full symmetric 8192 x 8192 Gram.  One step = the whole hot
-path: MPS build from the feature matrix (FP64, gate by gate; at reps = 2 stored
-as the three unit phases of every site) + the all-pairs contraction over the upper-triangle tiles
+path: MPS build from the feature matrix (FP64, gate by gate; in split FP32 at reps = 2 stored
+as the two gauged phases of every site) + the all-pairs contraction over the upper-triangle tiles
 (diagonal included) + the mirror write.  Entries counted = unique pairs
 contracted, N (N + 1) / 2 per step.
 
@@ -84,7 +84,7 @@ FMA_PER_CMAC = {"fp32": 4, "fp32_split": 12, "fp64": 4}
 # digest of the kernel sources it was captured on (kernel_digest()).  A configuration
 # not captured, or captured on other kernel sources, reports null.
 MEASURED_TRAFFIC_BYTES = {
-    ("gram_n784_r2_N8192", "fp32_split"): ("f539097c8c72144e", 13_559_001_600 + 549_287_424),
+    ("gram_n784_r2_N8192", "fp32_split"): ("2cfef18989c746a1", 13_557_435_392 + 549_152_000),
 }
 KERNEL_SOURCES = ("pair_contract.cuh", "pair_contract.cu", "qsvm_common.cuh")
 
