@@ -48,6 +48,20 @@ def test_reference_arm_under_torchrun():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
 
 
+def test_traffic_figure_follows_the_kernel_sources(monkeypatch):
+    """roofline.traffic is reported only while the pair-kernel sources are the ones its
+    ncu capture was taken on."""
+    sys.path.insert(0, ROOT)
+    import bench
+    key = ("gram_n784_r2_N8192", "fp32_split")
+    digest, nbytes = bench.MEASURED_TRAFFIC_BYTES[key]
+    monkeypatch.setattr(bench, "kernel_digest", lambda: digest)
+    assert bench.measured_traffic(*key) == nbytes
+    monkeypatch.setattr(bench, "kernel_digest", lambda: "0" * 16)
+    assert bench.measured_traffic(*key) is None
+    assert bench.measured_traffic("cfg1_n64_r2_N512x256", "fp32_split") is None
+
+
 @pytest.mark.gpu
 def test_gpu_arm_line():
     torch = pytest.importorskip("torch")
@@ -63,3 +77,9 @@ def test_gpu_arm_line():
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
     acc = d["accuracy_vs_oracle"]
     assert acc["max_abs_dK"] <= 1e-6 and acc["near_dup"]["max_abs_dK"] <= 1e-6
+    assert acc["near_dup"]["kernel"].startswith("qsvm_kernel_gram") and acc["near_dup"]["pairs_K_above_0.1"] > 0
+    p = d["pipeline"]
+    assert p["autotuned"] is True and p["configs_searched"] > 12 and "cta_pairs" in p
+    f64 = d["fp64_same_gpu"]
+    assert f64["tiles_timed"] == f64["tiles_total"] and f64["max_abs_dK_vs_fp64"] <= 1e-6
+    assert d["with_logK"]["entries_per_s"] > 0
