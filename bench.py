@@ -326,7 +326,9 @@ def run_ours(args):
     # pipeline shape: the autotuner times every shape on a Gram of up to 4096 of the
     # workload's points (untimed setup) and keeps the fastest for the timed steps
     pipeline = {"autotuned": False}
-    if not args.no_autotune:
+    if args.config is not None:  # a fixed configuration (e.g. the one the autotuner picked, for a profiler run)
+        qsvm.qsvm_set_config(reps, P, args.config)
+    elif not args.no_autotune:
         Nt = min(N, 4096)
         mps_t = torch.empty(qsvm.qsvm_mps_bytes(n, reps, Nt, P), dtype=torch.uint8, device=dev)
         qsvm.qsvm_build_mps(Xd[:Nt].contiguous(), reps, P, mps=mps_t, stream=stream)
@@ -747,6 +749,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the accuracy, FP64 and CPU side measurements")
     ap.add_argument("--sampled-fp64", action="store_true",
                     help="time the FP64 comparison path on the first 1/64 of the Gram's tiles only")
+    ap.add_argument("--config", type=int, default=None,
+                    help="run this pipeline configuration (qsvm_set_config index) instead of autotuning")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (by default it picks the pipeline shape and the pairs per CTA on up "
                          "to 4096 of the workload's points before timing)")

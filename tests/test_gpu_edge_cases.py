@@ -87,13 +87,20 @@ def test_wide_angle_range(q, oracle, prec, reps):
     assert np.max(np.abs(K.cpu().numpy() - Ko)) <= TOL[prec]
 
 
-def test_gram_offsets_beyond_32_bits(q, oracle):
+@pytest.mark.parametrize("quarter", [False, True])
+def test_gram_offsets_beyond_32_bits(q, oracle, quarter):
     """A 66 000-point Gram (n = 3, split FP32, a ragged last tile): K holds 4.36e9 entries,
     so its element offsets pass 2^32.  Sampled entries, many in the last rows, against the
-    oracle, and their mirrors bit-exact."""
+    oracle, and their mirrors bit-exact; with whole tiles per CTA and with quarter tiles
+    (a grid of 34 M CTAs)."""
     N, n, reps = 66000, 3, 2
     X = inputs.uniform_features(N, n, 123)
-    K, _ = q.gram(torch.from_numpy(X).cuda(), reps, "fp32_split", logK=False)  # K alone is 35 GB
+    if quarter:
+        q.qsvm_set_config(reps, "fp32_split", q.qsvm_num_configs() // 2 + 3)
+    try:
+        K, _ = q.gram(torch.from_numpy(X).cuda(), reps, "fp32_split", logK=False)  # K alone is 35 GB
+    finally:
+        q.qsvm_set_config(reps, "fp32_split", -1)
     torch.cuda.synchronize()
     assert q.qsvm_device_status() == 0
     rng = np.random.default_rng(5)
