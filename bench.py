@@ -79,12 +79,13 @@ def dense_cmacs_per_entry(n: int, reps: int) -> int:
 FMA_PER_CMAC = {"fp32": 4, "fp32_split": 12, "fp64": 4}
 
 # DRAM bytes (read + write) of one pair-kernel launch, from one ncu capture of the
-# same configuration with the default pipeline shape (dram__bytes_read.sum +
+# same workload, precision and pipeline configuration (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass over the full-size launch), each stored with the
-# digest of the kernel sources it was captured on (kernel_digest()).  A configuration
-# not captured, or captured on other kernel sources, reports null.
+# digest of the kernel sources it was captured on (kernel_digest()).  A workload or
+# configuration not captured, or captured on other kernel sources, reports null.
 MEASURED_TRAFFIC_BYTES = {
-    ("gram_n784_r2_N8192", "fp32_split"): ("2cfef18989c746a1", 13_557_435_392 + 549_152_000),
+    ("gram_n784_r2_N8192", "fp32_split", 9): ("2d0ed45235169d41", 2_709_482_752 + 551_164_928),
+    ("cfg4_n784_r3_N8192", "fp32_split", 20): ("2d0ed45235169d41", 4_013_184_768 + 566_748_416),
 }
 KERNEL_SOURCES = ("pair_contract.cuh", "pair_contract.cu", "qsvm_common.cuh")
 
@@ -99,8 +100,8 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload: str, prec: str):
-    entry = MEASURED_TRAFFIC_BYTES.get((workload, prec))
+def measured_traffic(workload: str, prec: str, config: int):
+    entry = MEASURED_TRAFFIC_BYTES.get((workload, prec, config))
     if entry is None or entry[0] != kernel_digest():
         return None
     return entry[1]
@@ -435,7 +436,7 @@ def run_ours(args):
         bound = "alu"
     fma_frac = (FMA_PER_CMAC[prec] * 2.0 * cm * pairs_rank / (kms * 1e-3) / 1e12) / peak
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": measured_traffic(args.workload, prec) if world == 1 else None,
+                "traffic": measured_traffic(args.workload, prec, cfg) if world == 1 else None,
                 "traffic_unit": "bytes per launch (ncu)",
                 "kernel_digest": kernel_digest(),
                 "kernel": f"pair_tile_kernel<chi={2 ** reps},{prec}>",

@@ -53,13 +53,14 @@ def test_traffic_figure_follows_the_kernel_sources(monkeypatch):
     ncu capture was taken on."""
     sys.path.insert(0, ROOT)
     import bench
-    key = ("gram_n784_r2_N8192", "fp32_split")
+    key = ("gram_n784_r2_N8192", "fp32_split", 9)
     digest, nbytes = bench.MEASURED_TRAFFIC_BYTES[key]
     monkeypatch.setattr(bench, "kernel_digest", lambda: digest)
     assert bench.measured_traffic(*key) == nbytes
+    assert bench.measured_traffic("gram_n784_r2_N8192", "fp32_split", 3) is None  # another configuration
+    assert bench.measured_traffic("cfg1_n64_r2_N512x256", "fp32_split", 9) is None
     monkeypatch.setattr(bench, "kernel_digest", lambda: "0" * 16)
     assert bench.measured_traffic(*key) is None
-    assert bench.measured_traffic("cfg1_n64_r2_N512x256", "fp32_split") is None
 
 
 @pytest.mark.gpu

@@ -98,12 +98,14 @@ def test_every_config_bit_identical(q, reps):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_split", "fp32"])
 @pytest.mark.parametrize("reps", [1, 2, 3])
-def test_quarter_tile_configs_vs_oracle(q, oracle, prec, reps):
+@pytest.mark.parametrize("N,Nt", [(37, 21), (1, 1), (9, 5)])
+def test_quarter_tile_configs_vs_oracle(q, oracle, prec, reps, N, Nt):
     """Configurations that give each CTA a quarter of a tile: Gram and cross kernel with
     ragged edges (quarters beyond the last row or column, the skipped quarter below a
-    diagonal tile) against the oracle, and bit-identical to the whole-tile default."""
+    diagonal tile; a single point) against the oracle, and bit-identical to the
+    whole-tile default."""
     tol = {"fp64": 1e-10, "fp32_split": 1e-6, "fp32": 2e-5}[prec]
-    n, N, Nt = 13, 37, 21
+    n = 13
     X, Xt = inputs.uniform_features(N, n, 61), inputs.uniform_features(Nt, n, 62)
     Ko, _ = oracle.mps_gram(X, reps)
     Kxo, _ = oracle.mps_cross(Xt, X, reps)

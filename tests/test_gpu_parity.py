@@ -290,7 +290,7 @@ def test_near_duplicates_n784(q, oracle, prec):
     assert err <= tol, f"{prec}: max|dK| = {err:.3e}"
 
 
-@pytest.mark.parametrize("prec,reps", [("fp64", 2), ("fp32_split", 2), ("fp32_split", 3)])
+@pytest.mark.parametrize("prec,reps", [("fp64", 2), ("fp32_split", 2), ("fp32_split", 3), ("fp64", 3), ("fp32", 2)])
 def test_gram_near_duplicate_clusters_n784(q, oracle, prec, reps):
     """The symmetric Gram kernel (not the cross kernel) where |dK| <= 1e-6 bites: 24
     MNIST-like base rows with three perturbed copies each, shuffled, so that pairs with
@@ -310,10 +310,14 @@ def test_gram_near_duplicate_clusters_n784(q, oracle, prec, reps):
     Kg, LKg = K.cpu().numpy(), LK.cpu().numpy()
     assert q.qsvm_device_status() == 0
     assert np.array_equal(Kg, Kg.T) and np.array_equal(LKg, LKg.T)
-    _check(Kg, Ko, prec, f"near-duplicate Gram reps={reps}", LKg, LKo)
+    tol = 1e-4 if prec == "fp32" else TOL[prec]  # plain FP32's coherent rounding at n = 784
+    err = np.max(np.abs(Kg - Ko))
+    assert err <= tol, f"near-duplicate Gram {prec} reps={reps}: max|dK| = {err:.3e}"
+    m = Ko > 1e-300
+    assert np.max(np.abs(LKg[m] - LKo[m])) <= (1e-2 if prec == "fp32" else LOG_TOL[prec])
     # the informative entries on their own, in both kinds of tile
     for m in (big & same_tile, big & ~same_tile):
-        assert np.max(np.abs(Kg[I[m], J[m]] - Ko[I[m], J[m]])) <= TOL[prec]
+        assert np.max(np.abs(Kg[I[m], J[m]] - Ko[I[m], J[m]])) <= tol
 
 
 def test_reps3_n784_logk(q, oracle):
