@@ -1153,11 +1153,6 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
 
   __device__ __forceinline__ void site(uint32_t ra, uint32_t rb) {
     const float2 m1 = make_float2(-1.f, -1.f);
-    SplitForm R[2];
-    split_rho(ra + Rec::off(0, 0), ra + Rec::off(0, 1), rb + Rec::off(0, 0), rb + Rec::off(0, 1), R[0].h, R[0].ih,
-              R[0].l, R[0].il);
-    split_rho(ra + Rec::off(1, 0), ra + Rec::off(1, 1), rb + Rec::off(1, 0), rb + Rec::off(1, 1), R[1].h, R[1].ih,
-              R[1].l, R[1].il);
     // ---- rows of column t: Y_c = (M_i x M_i)^T Ev_c, X_s = Y_0 + rho_s Y_1 ----
     float2 Xh[2][H], Xl[2][H];
     {
@@ -1198,13 +1193,17 @@ struct QuadEngine<QSVM_FP32_SPLIT> {
           }
       }
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < 2; ++s) {
+        SplitForm R;  // rho_s, formed where it is used (one live at a time)
+        split_rho(ra + Rec::off(s, 0), ra + Rec::off(s, 1), rb + Rec::off(s, 0), rb + Rec::off(s, 1), R.h, R.ih, R.l,
+                  R.il);
 #pragma unroll
         for (int p = 0; p < H; ++p) {
           float2 hh = Y0h[p], ll = Y0l[p], xf;
-          smac(hh, ll, Y1h[p], Y1l[p], Y1f[p], R[s]);
+          smac(hh, ll, Y1h[p], Y1l[p], Y1f[p], R);
           ssplit<GX>(hh, ll, Xh[s][p], Xl[s][p], xf);
         }
+      }
     }
     // ---- X changes hands: thread t takes row p = t of both X_s ----
     __syncwarp(mask);  // every thread has read the previous site's environment entries
