@@ -165,6 +165,9 @@ int32_t qsvm_build_mps(const double* X, int64_t n_points, int32_t n_qubits, int3
  *   K     device float64, n_points rows, ldk >= n_points.
  *   logK  device float64 or NULL; if given, ln K (-inf where the amplitude is 0);
  *         ldl >= n_points.  K underflows to 0 below ~1e-308 while logK stays exact.
+ * No workspace: each pair's environment lives in registers (or, at reps = 3 in
+ * split FP32, in the CTA's shared memory) for the whole chain, and tiles write
+ * their results straight into K, so the call takes no scratch argument.
  * Errors: QSVM_ERR_ARG, QSVM_ERR_CHI, QSVM_ERR_CUDA. */
 int32_t qsvm_kernel_gram(const void* mps, int64_t n_points, int32_t n_qubits, int32_t reps, int32_t precision,
                          double* K, int64_t ldk, double* logK, int64_t ldl, void* stream);
