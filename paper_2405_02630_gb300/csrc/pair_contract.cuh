@@ -958,16 +958,16 @@ struct Engine<4, QSVM_FP32_SPLIT> {
     for (int s = 0; s < 2; ++s) {
       // X_s = Y_0 + rho_s Y_1, then E'_s = X_s conj(b); rho_s is formed here, so that
       // only one of the two is live at a time (0.7 % faster than forming both first)
-      SplitForm R[2];
-      split_rho(ra + Rec::off(s, 0), ra + Rec::off(s, 1), rb + Rec::off(s, 0), rb + Rec::off(s, 1), R[s].h, R[s].ih,
-                R[s].l, R[s].il);
+      SplitForm R;
+      split_rho(ra + Rec::off(s, 0), ra + Rec::off(s, 1), rb + Rec::off(s, 0), rb + Rec::off(s, 1), R.h, R.ih, R.l,
+                R.il);
       float2 Xh[2][2], Xl[2][2], Xf[2][2];
 #pragma unroll
       for (int p = 0; p < 2; ++p)
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           float2 hh = Y0h[p][r], ll = Y0l[p][r];
-          smac(hh, ll, Y1h[p][r], Y1l[p][r], Y1f[p][r], R[s]);
+          smac(hh, ll, Y1h[p][r], Y1l[p][r], Y1f[p][r], R);
           if (r) {
             ssplit(hh, ll, Cg, Xh[p][r], Xl[p][r], Xf[p][r]);
           } else {  // seeds E'_s[p][.]
