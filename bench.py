@@ -84,8 +84,8 @@ FMA_PER_CMAC = {"fp32": 4, "fp32_split": 12, "fp64": 4}
 # digest of the kernel sources it was captured on (kernel_digest()).  A workload or
 # configuration not captured, or captured on other kernel sources, reports null.
 MEASURED_TRAFFIC_BYTES = {
-    ("gram_n784_r2_N8192", "fp32_split", 9): ("aec0a6d100cf465a", 2_655_056_128 + 549_486_080),
-    ("cfg4_n784_r3_N8192", "fp32_split", 20): ("aec0a6d100cf465a", 4_011_472_640 + 565_071_872),
+    ("gram_n784_r2_N8192", "fp32_split", 9): ("e5bc5932b71cb763", 2_660_363_776 + 550_344_448),
+    ("cfg4_n784_r3_N8192", "fp32_split", 20): ("e5bc5932b71cb763", 4_014_598_400 + 567_146_240),
 }
 KERNEL_SOURCES = ("pair_contract.cuh", "pair_contract.cu", "qsvm_common.cuh")
 
