@@ -39,7 +39,9 @@ def _jobs(q, specs, reps, prec, seed, logk=True):
 SPECS = [(37, 16), (80, 64), (17, 130), (64, 16), (5, 64), (33, 40)]
 
 
-@pytest.mark.parametrize("prec,reps", [("fp64", 2), ("fp32_split", 2), ("fp32", 2), ("fp32_split", 3), ("fp64", 3), ("fp64", 1)])
+# every compiled persistent kernel: chi = 2, 4, 8 (reps 1, 2, 3) in each precision
+@pytest.mark.parametrize("prec,reps", [("fp64", 2), ("fp32_split", 2), ("fp32", 2), ("fp32_split", 3), ("fp64", 3),
+                                       ("fp32", 3), ("fp64", 1), ("fp32_split", 1), ("fp32", 1)])
 def test_batch_matches_per_job_gram(q, oracle, prec, reps):
     jobs, Xs = _jobs(q, SPECS, reps, prec, 1)
     ws = torch.empty(q.qsvm_batch_workspace_bytes(len(jobs)), dtype=torch.uint8, device="cuda")
